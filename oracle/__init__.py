@@ -1,0 +1,140 @@
+"""FP64 CPU oracle for the iterated 5-point Jacobi-2D stencil.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg (and its ``--impl reference`` arm) may import
+this package.  The CUDA library never calls it, and the two share no code:
+this wrapper loads ``jacobi2d_oracle.c`` compiled by gcc with
+``-O2 -ffp-contract=off`` (no fast-math), nothing else.
+
+What it computes is the plain definition (paper Sec. 6.1, Jacobi stencil;
+Fig. 1 for the ping-pong state loop; Sec. 3 "State" for the data-dependent
+stop condition); the C file's header spells out the formula and each reading
+of a point the paper leaves open.
+
+``jacobi2d_window`` adds one more exact use of the definition: one timestep
+moves information by one cell, so the grid after T steps inside a window
+depends only on the input within distance T of it.  Running the definition on
+a crop that extends T+1 cells past the window (clamped to the grid) therefore
+gives the window's values exactly, whatever the crop's artificial edge does.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+(hand-computed 4x4 fixtures, exact rational brute force, closed-form
+eigenmodes, harmonic fixed points, maximum principle, symmetries, semigroup,
+thread-count invariance, closed-form stopping step) and by mutation tests that
+plant mistakes in a copy of the C source and check the pins catch them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "jacobi2d_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c99"]
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle C source file to a shared object with the oracle's flags."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *CFLAGS, "-o", tmp, src, "-lm"], check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Build liboracle.so (only if missing or older than the source)."""
+    with _lock:
+        if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+            compile_source(_SRC, _LIB_PATH)
+    return _LIB_PATH
+
+
+def load_library(path: str) -> ctypes.CDLL:
+    lib = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lp = ctypes.POINTER(ctypes.c_long)
+    lib.oracle_jacobi2d.argtypes = [dp, dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_int]
+    lib.oracle_jacobi2d.restype = ctypes.c_int
+    lib.oracle_jacobi2d_tol.argtypes = [dp, dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double,
+                                        ctypes.c_long, ctypes.c_int, lp, dp, dp]
+    lib.oracle_jacobi2d_tol.restype = ctypes.c_int
+    lib.oracle_num_threads.argtypes = [ctypes.c_int]
+    lib.oracle_num_threads.restype = ctypes.c_int
+    return lib
+
+
+def _get():
+    global _lib
+    if _lib is None:
+        _lib = load_library(build())
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _as_f64(grid) -> np.ndarray:
+    g = np.ascontiguousarray(np.asarray(grid, dtype=np.float64))
+    if g.ndim != 2:
+        raise ValueError("grid must be 2-D")
+    return g
+
+
+def num_threads(threads: int = 0, lib=None) -> int:
+    """Threads the oracle uses for ``threads`` (0 = OpenMP default)."""
+    return int((lib or _get()).oracle_num_threads(int(threads)))
+
+
+def jacobi2d(grid, T: int, threads: int = 1, lib=None) -> np.ndarray:
+    """Grid after T timesteps (FP64; the input is converted to FP64 exactly)."""
+    lib = lib or _get()
+    a = _as_f64(grid)
+    out = np.empty_like(a)
+    rc = lib.oracle_jacobi2d(_dptr(a), _dptr(out), a.shape[0], a.shape[1], int(T), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_jacobi2d failed with status {rc}")
+    return out
+
+
+def jacobi2d_tol(grid, T_cap: int, tol: float, check_stride: int, threads: int = 1, lib=None):
+    """Tolerance mode.  Returns (grid, steps_done, rel_residual, r_first)."""
+    lib = lib or _get()
+    a = _as_f64(grid)
+    out = np.empty_like(a)
+    steps = ctypes.c_long(0)
+    rel = ctypes.c_double(0.0)
+    r1 = ctypes.c_double(0.0)
+    rc = lib.oracle_jacobi2d_tol(_dptr(a), _dptr(out), a.shape[0], a.shape[1], int(T_cap), float(tol),
+                                 int(check_stride), int(threads), ctypes.byref(steps), ctypes.byref(rel),
+                                 ctypes.byref(r1))
+    if rc != 0:
+        raise ValueError(f"oracle_jacobi2d_tol failed with status {rc}")
+    return out, int(steps.value), float(rel.value), float(r1.value)
+
+
+def jacobi2d_window(grid, T: int, r0: int, r1: int, c0: int, c1: int, threads: int = 1, lib=None) -> np.ndarray:
+    """Rows r0:r1, cols c0:c1 of the grid after T steps, from a light-cone crop.
+
+    A window cell at distance > T from the crop's artificial edge cannot be
+    reached by anything the crop gets wrong, so the result is exact.
+    """
+    a = np.asarray(grid)
+    R, C = a.shape
+    if not (0 <= r0 <= r1 <= R and 0 <= c0 <= c1 <= C):
+        raise ValueError("window out of range")
+    m = int(T) + 1
+    cr0, cr1 = max(0, r0 - m), min(R, r1 + m)
+    cc0, cc1 = max(0, c0 - m), min(C, c1 + m)
+    crop = jacobi2d(a[cr0:cr1, cc0:cc1], T, threads=threads, lib=lib)
+    return crop[r0 - cr0:r1 - cr0, c0 - cc0:c1 - cc0]

@@ -1,0 +1,55 @@
+"""Plants plausible mistakes in a copy of the oracle's C source (on the CPU)
+and checks that the pins of ``test_oracle_pins`` catch every one of them.
+
+Each mutant is a single textual edit of ``oracle/jacobi2d_oracle.c``: a
+dropped term, a wrong sign, a wrong neighbour index, a transposed extent, a
+wrong weight, an in-place update instead of ping-pong, a written boundary, an
+off-by-one step count, and mistakes in the residual / stopping rule.
+"""
+import os
+
+import pytest
+
+import oracle
+from tests.test_oracle_pins import ALL_PINS
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "jacobi2d_oracle.c")
+
+MUTANTS = {
+    "drop_centre": ("double sum = centre + (ns + we);", "double sum = (ns + we);"),
+    "sign_east": ("row[j - 1] + row[j + 1]", "row[j - 1] - row[j + 1]"),
+    "south_index": ("north[j] + south[j]", "north[j] + south[j + 1]"),
+    "west_index": ("row[j - 1] + row[j + 1]", "row[j] + row[j + 1]"),
+    "transposed_extent": ("for (i = 1; i < R - 1; ++i) {\n        const double *north",
+                          "for (i = 1; i < (C < R ? C : R) - 1; ++i) {\n        const double *north"),
+    "weight": ("dst[j] = 0.2 * sum;", "dst[j] = 0.25 * sum;"),
+    "in_place": ("        oracle_step(A, B, R, C, nth);\n        tmp = A;",
+                 "        oracle_step(A, A, R, C, nth);\n        tmp = A;"),
+    "boundary_written": ("for (j = 1; j < C - 1; ++j) {\n            double centre",
+                         "for (j = 1; j < C; ++j) {\n            double centre"),
+    "off_by_one_T": ("for (t = 1; t <= T; ++t)", "for (t = 1; t < T; ++t)"),
+    "residual_squared": ("rel = (r1 > 0.0) ? rt / r1 : 0.0;", "rel = (r1 > 0.0) ? (rt * rt) / (r1 * r1) : 0.0;"),
+    "residual_wrong_pair": ("rt = sqrt(oracle_sqdiff(B, A, R, C, rowsum, nth));",
+                            "rt = sqrt(oracle_sqdiff(B, B, R, C, rowsum, nth));"),
+    "check_phase": ("int is_check = (t % check_stride) == 0;", "int is_check = (t % check_stride) == 1;"),
+    "stop_rule": ("if (is_check && tol > 0.0 && rel <= tol)", "if (is_check && tol > 0.0 && rel < tol * tol)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    mutated = src.replace(old, new, 1)
+    path = tmp_path / f"mut_{name}.c"
+    path.write_text(mutated)
+    so = oracle.compile_source(str(path), str(tmp_path / f"libmut_{name}.so"))
+    lib = oracle.load_library(so)
+    caught = []
+    for pin in ALL_PINS:
+        try:
+            pin(lib)
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, f"no pin caught mutant {name}"
