@@ -1,0 +1,217 @@
+/*
+ * sdfg_jacobi.h -- C ABI of libsdfgjacobi.so: the iterated 5-point Jacobi-2D
+ * stencil on one GB300 (sm_103a), single grids, batches of uneven grids, and
+ * a continuous-batching server.
+ *
+ * The operation (paper Sec. 6.1, "Jacobi Stencil": a 5-point stencil applied
+ * repeatedly for T iterations on a 2-D domain with constant boundary
+ * conditions; Fig. 1: a state loop over a map that ping-pongs between two
+ * copies of the array; Appendix A: one state (timestep) completes before the
+ * next begins):
+ *
+ *   for t = 1..T:  B[i][j] = 0.2 * (A[i][j] + ((A[i-1][j] + A[i+1][j])
+ *                                              + (A[i][j-1] + A[i][j+1])))
+ *                  for 1 <= i <= rows-2, 1 <= j <= cols-2;  then A <- B.
+ *
+ * The boundary ring (row 0, row rows-1, column 0, column cols-1) keeps its
+ * input values for ever (Dirichlet).  The result is the full grid after T
+ * steps, boundary included.  Every update is evaluated in the order shown,
+ * with IEEE round-to-nearest and no fused multiply-add, so FP32 and FP64
+ * results do not depend on tiling, on the number of fused steps, or on what
+ * else runs in the same batch.  FP64 results equal a plain FP64 loop bit for
+ * bit.
+ *
+ * Storage types: FP32 (arithmetic FP32), BF16 (arithmetic FP32; every
+ * timestep's result is rounded to BF16 with round-to-nearest-even, as if the
+ * array were written back after each step), FP64 (arithmetic FP64).
+ *
+ * Layout: row-major, `ld` elements between the starts of consecutive rows
+ * (ld >= cols).  All grid pointers are DEVICE pointers unless a function says
+ * otherwise.  `in` and `out` must either be the same pointer (in place) or
+ * not overlap.  The fastest path needs 16-byte aligned pointers and
+ * ld * sizeof(element) a multiple of 16; other layouts are staged through an
+ * aligned internal copy (correct, slower).
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Functions described as asynchronous only enqueue work and return.
+ *
+ * Ownership: the caller owns every grid and descriptor.  The library owns
+ * only its scratch (stream-ordered allocations it frees itself) and the
+ * server's internal copies of descriptors.
+ *
+ * Errors: every function returns an sdfg_status.  Argument errors are found
+ * on the host before any work is enqueued.  Errors of the CUDA runtime are
+ * returned as SDFG_ERR_CUDA.  A device-side wait that runs out (persistent
+ * kernels) records SDFG_ERR_TIMEOUT in a per-device error word, which
+ * sdfg_device_error() reads.  sdfg_last_error() returns a thread-local
+ * message about the most recent failure on the calling thread.
+ */
+#ifndef SDFG_JACOBI_H
+#define SDFG_JACOBI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { SDFG_F32 = 0, SDFG_BF16 = 1, SDFG_F64 = 2 } sdfg_dtype;
+
+typedef enum {
+    SDFG_OK = 0,
+    SDFG_PENDING = 1,           /* server request not finished yet           */
+    SDFG_ERR_INVAL = -1,        /* bad argument                              */
+    SDFG_ERR_NOMEM = -2,        /* device allocation failed / over budget    */
+    SDFG_ERR_CUDA = -3,         /* CUDA runtime or driver error              */
+    SDFG_ERR_TIMEOUT = -4,      /* a bounded wait ran out                    */
+    SDFG_ERR_BUSY = -5,         /* object in use / shutting down             */
+    SDFG_ERR_UNSUPPORTED = -6   /* no GPU of the required architecture       */
+} sdfg_status;
+
+/* Kernel families for sdfg_config.kernel. */
+typedef enum {
+    SDFG_KERNEL_AUTO = 0,       /* autotuned choice                          */
+    SDFG_KERNEL_NAIVE = 1,      /* one timestep per launch, one thread/point */
+    SDFG_KERNEL_TEMPORAL = 2,   /* k timesteps per launch (one pass)         */
+    SDFG_KERNEL_PERSISTENT = 3  /* one launch for all passes, dependency-driven */
+} sdfg_kernel;
+
+/*
+ * Execution configuration (all fields 0 = choose automatically).
+ *   k          timesteps fused per pass: 1, 2, 4 or 8 (paper App. B,
+ *              StateFusion/MapToForLoop applied to the timestep loop);
+ *   seg_rows   output rows per work unit (MapTiling along rows);
+ *   warps      warps per CTA.
+ */
+typedef struct {
+    int kernel;
+    int k;
+    int seg_rows;
+    int warps;
+} sdfg_config;
+
+/*
+ * Single grid, FP32, asynchronous.  in/out: device pointers to rows x cols
+ * floats, ld = cols.  T >= 0 timesteps (T = 0 copies).  rows, cols >= 0; a
+ * grid with fewer than 3 rows or columns has no interior and is copied.
+ */
+int sdfg_jacobi2d(const float *in, float *out, int rows, int cols, int T, void *stream);
+
+/* Same for any storage type (sdfg_dtype) and pitch ld (elements). */
+int sdfg_jacobi2d_ex(const void *in, void *out, int rows, int cols, int ld, int T, int dtype,
+                     void *stream);
+
+/* Same with an explicit configuration (cfg may be NULL = automatic). */
+int sdfg_jacobi2d_cfg(const void *in, void *out, int rows, int cols, int ld, int T, int dtype,
+                      const sdfg_config *cfg, void *stream);
+
+/*
+ * End-to-end call on HOST buffers (contiguous, ld = cols): copies h_in to the
+ * device, runs T steps, copies the result to h_out, and returns when h_out
+ * holds it.  Pinned host memory gives the fastest copies.  Device buffers are
+ * cached by the library between calls of the same size.
+ */
+int sdfg_jacobi2d_host(const void *h_in, void *h_out, int rows, int cols, int T, int dtype,
+                       void *stream);
+
+/*
+ * One solve, as used by the batch and the server.  Inputs: in, out, rows,
+ * cols, ld, T (the step cap), tol, dtype.  tol = 0 runs exactly T steps.
+ * tol > 0 stops at the first step t that is a multiple of the check stride
+ * with rel_t <= tol, where rel_t = ||A_t - A_{t-1}||_2 / ||A_1 - A_0||_2 over
+ * the interior (paper Sec. 3 "State": a transition condition that depends on
+ * data).  Squared differences are formed in the storage precision's
+ * arithmetic (FP32 for FP32/BF16) and summed in groups of at most 32 terms
+ * in FP32; every further level of the reduction is FP64 in a fixed order.
+ * Outputs: status, steps_done, rel_residual (rel at the final step).
+ */
+typedef struct {
+    const void *in;
+    void *out;
+    int rows, cols, ld;
+    int T;
+    double tol;
+    int dtype;
+    int status;
+    int steps_done;
+    double rel_residual;
+} sdfg_desc;
+
+/* Single-grid solve with tolerance; blocks until the outputs are filled. */
+int sdfg_jacobi2d_solve(sdfg_desc *desc, int check_stride, const sdfg_config *cfg, void *stream);
+
+/*
+ * Batch of n independent grids in ONE persistent launch (paper Sec. 3,
+ * Consume scope: workers dequeue units from a shared work list with atomics).
+ * Blocks until done and fills every descriptor's outputs.  All descriptors
+ * must share one dtype.  check_stride applies to descriptors with tol > 0.
+ */
+int sdfg_jacobi2d_batch(sdfg_desc *desc, int n, int check_stride, void *stream);
+
+/*
+ * Batch plans: build once, replay many times.  The plan captures the
+ * persistent launch (and its staging/finalise steps) in a CUDA graph.
+ * plan_run is asynchronous; plan_results waits for the last run and fills
+ * the outputs of desc[0..n-1] (the same order as at creation).
+ */
+typedef struct sdfg_batch_plan sdfg_batch_plan;
+int sdfg_batch_plan_create(sdfg_batch_plan **plan, const sdfg_desc *desc, int n, int check_stride,
+                           const sdfg_config *cfg, void *stream);
+int sdfg_batch_plan_run(sdfg_batch_plan *plan, void *stream);
+int sdfg_batch_plan_results(sdfg_batch_plan *plan, sdfg_desc *desc, int n);
+int sdfg_batch_plan_destroy(sdfg_batch_plan *plan);
+
+/*
+ * Continuous-batching server.  Requests (sdfg_desc, tol > 0 or a fixed T)
+ * are admitted while the sum of their device footprints stays within
+ * hbm_budget_bytes and fewer than max_slots are active; every wave advances
+ * all active grids by quantum_steps steps (or to their stop) in one
+ * persistent launch; finished grids retire between waves and queued requests
+ * take their place.  quantum_steps must be a multiple of check_stride.
+ * The caller keeps each request's in/out alive until poll reports it done.
+ */
+typedef struct sdfg_server sdfg_server;
+int sdfg_server_create(sdfg_server **server, size_t hbm_budget_bytes, int max_slots, int quantum_steps,
+                       int check_stride, int device);
+int sdfg_server_submit(sdfg_server *server, const sdfg_desc *desc, uint64_t *req_id);
+/* SDFG_PENDING while running; SDFG_OK or an error once done (result filled). */
+int sdfg_server_poll(sdfg_server *server, uint64_t req_id, sdfg_desc *result);
+/* Waits until every submitted request is done; SDFG_ERR_TIMEOUT on expiry. */
+int sdfg_server_drain(sdfg_server *server, int timeout_ms);
+int sdfg_server_destroy(sdfg_server *server);
+
+/* Autotuner: times candidate configurations for this shape and dtype on the
+ * calling stream, caches the best by shape class, and returns it. */
+int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *best, void *stream);
+
+/* Per-kernel CUDA-event timing inside the library (off by default).  While
+ * enabled, every launch is bracketed by events on its own stream. */
+int sdfg_stats_enable(int on);
+int sdfg_stats_reset(void);
+/* Sums over launches of kernel family `name` ("naive", "temporal",
+ * "persistent", "reduce", "copy"); waits for the recorded events. */
+int sdfg_stats_get(const char *name, long long *launches, double *total_ms);
+
+/* Reads (and with clear != 0 resets) the current device's error word. */
+int sdfg_device_error(int clear);
+
+/* Thread-local description of the last failure on this thread. */
+const char *sdfg_last_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int sdfg_version(void);
+
+/*
+ * Host-only planning query (no GPU needed): the work decomposition the
+ * temporal and persistent kernels use for a grid.  info[0..7] receives
+ * {halo_cols, warp_cols, out_cols_per_strip, n_strips, seg_rows, n_segs,
+ *  chunk_rows, stages}.
+ */
+int sdfg_plan_geometry(int rows, int cols, int dtype, int k, int seg_rows, int *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDFG_JACOBI_H */

@@ -1,0 +1,212 @@
+// Single-grid entry points: sdfg_jacobi2d, _ex, _cfg, _host.
+//
+// The timestep loop is a sequence of passes (paper Fig. 1: a state loop whose
+// body is a map; App. B StateFusion fuses k states into one pass).  Pass p
+// reads buffer src_p and writes dst_p; the buffers alternate between the
+// caller's `out` and one scratch grid, arranged so that the last pass writes
+// `out` whenever `in` and `out` differ.
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "autotune.h"
+#include "runtime.h"
+
+namespace sdfg {
+
+int validate_grid(const void *in, const void *out, int R, int C, int ld, long long T, int dtype, const char *who) {
+    if (!dtype_valid(dtype)) return set_error(SDFG_ERR_INVAL, "%s: unknown dtype %d", who, dtype);
+    if (R < 0 || C < 0) return set_error(SDFG_ERR_INVAL, "%s: rows=%d cols=%d must be >= 0", who, R, C);
+    if (T < 0) return set_error(SDFG_ERR_INVAL, "%s: T=%lld must be >= 0", who, T);
+    if (R > 0 && C > 0) {
+        if (ld < C) return set_error(SDFG_ERR_INVAL, "%s: ld=%d < cols=%d", who, ld, C);
+        if (!in || !out) return set_error(SDFG_ERR_INVAL, "%s: null grid pointer", who);
+        const size_t S = dtype_bytes(dtype);
+        const char *a = static_cast<const char *>(in);
+        const char *b = static_cast<const char *>(out);
+        const size_t span = (static_cast<size_t>(R - 1) * ld + C) * S;
+        if (a != b && a < b + span && b < a + span)
+            return set_error(SDFG_ERR_INVAL, "%s: in and out overlap without being the same grid", who);
+        if (reinterpret_cast<uintptr_t>(in) % S || reinterpret_cast<uintptr_t>(out) % S)
+            return set_error(SDFG_ERR_INVAL, "%s: grid pointers must be aligned to the element size", who);
+    }
+    return SDFG_OK;
+}
+
+int resolve_config(const sdfg_config *cfg, int R, int C, int dtype, sdfg_config *out) {
+    sdfg_config c = {SDFG_KERNEL_AUTO, 0, 0, 0};
+    if (cfg) c = *cfg;
+    if (c.kernel < SDFG_KERNEL_AUTO || c.kernel > SDFG_KERNEL_PERSISTENT)
+        return set_error(SDFG_ERR_INVAL, "unknown kernel family %d", c.kernel);
+    if (c.k != 0 && !depth_supported(c.k)) return set_error(SDFG_ERR_INVAL, "k=%d not supported (1, 2, 4, 8)", c.k);
+    if (c.seg_rows < 0 || c.warps < 0 || c.warps > MAX_WARPS)
+        return set_error(SDFG_ERR_INVAL, "bad seg_rows/warps (%d/%d)", c.seg_rows, c.warps);
+    sdfg_config tuned;
+    const bool have = autotune_lookup(R, C, dtype, &tuned);
+    if (c.kernel == SDFG_KERNEL_AUTO) c.kernel = have ? tuned.kernel : SDFG_KERNEL_TEMPORAL;
+    if (c.k == 0) c.k = have && tuned.k ? tuned.k : default_depth(dtype);
+    if (c.warps == 0) c.warps = have && tuned.warps ? tuned.warps : 8;
+    if (c.seg_rows == 0 && have) c.seg_rows = tuned.seg_rows;
+    *out = c;
+    return SDFG_OK;
+}
+
+// Run the passes `ks` on (src0 -> ... ) alternating between buffers `first`
+// and `second`; returns the buffer holding the result in *final.
+static int run_pass_sequence(const void *src0, void *first, void *second, const std::vector<int> &ks, int R, int C,
+                             int ld, int dtype, const sdfg_config &c, DeviceState *st, cudaStream_t s,
+                             void **final) {
+    *final = const_cast<void *>(src0);
+    if (ks.empty()) return SDFG_OK;
+    if (c.kernel == SDFG_KERNEL_NAIVE) {
+        const void *src = src0;
+        void *dst = first;
+        for (size_t p = 0; p < ks.size(); ++p) {
+            for (int t = 0; t < ks[p]; ++t) {
+                int rc = launch_naive_step(src, dst, R, C, ld, dtype, s);
+                if (rc != SDFG_OK) return rc;
+                src = dst;
+                dst = (dst == first) ? second : first;
+            }
+        }
+        *final = const_cast<void *>(src);
+        return SDFG_OK;
+    }
+    const int S = dtype_bytes(dtype);
+    const int W = 32 * lane_cols(S);
+    const int bps = std::max(1, temporal_blocks_per_sm(dtype, c.k, c.warps));
+    const GridGeo g = plan_geometry(R, C, ld, dtype, c.k, c.seg_rows, static_cast<long long>(st->sm_count) * bps * c.warps);
+    alignas(64) CUtensorMap tm_src0, tm_first, tm_second;
+    int rc = encode_tmap(&tm_src0, src0, dtype, R, C, ld, W);
+    if (rc == SDFG_OK) rc = encode_tmap(&tm_first, first, dtype, R, C, ld, W);
+    if (rc == SDFG_OK) rc = encode_tmap(&tm_second, second, dtype, R, C, ld, W);
+    if (rc != SDFG_OK) return rc;
+    const CUtensorMap *tm_src = &tm_src0;
+    void *dst = first;
+    for (size_t p = 0; p < ks.size(); ++p) {
+        rc = launch_temporal_pass(tm_src, dst, g, dtype, ks[p], c.warps, 0, nullptr, st->d_err, DEFAULT_TIMEOUT_NS, s);
+        if (rc != SDFG_OK) return rc;
+        *final = dst;
+        tm_src = (dst == first) ? &tm_first : &tm_second;
+        dst = (dst == first) ? second : first;
+    }
+    return SDFG_OK;
+}
+
+// Core single-grid run.  in_disposable: `in` may be overwritten (it then
+// serves as the scratch grid).
+int run_single(const void *in, void *out, int R, int C, int ld, long long T, int dtype, const sdfg_config *cfg,
+               bool in_disposable, cudaStream_t s) {
+    if (R == 0 || C == 0) return SDFG_OK;
+    DeviceState *st = nullptr;
+    int rc = current_device(&st);
+    if (rc != SDFG_OK) return rc;
+    if (T == 0 || R < 3 || C < 3) return launch_copy2d(out, ld, in, ld, R, C, dtype, s);
+    sdfg_config c;
+    rc = resolve_config(cfg, R, C, dtype, &c);
+    if (rc != SDFG_OK) return rc;
+    const std::vector<int> ks = c.kernel == SDFG_KERNEL_NAIVE ? std::vector<int>(1, static_cast<int>(T))
+                                                              : plan_passes(T, c.k);
+    const long long n_steps_total = c.kernel == SDFG_KERNEL_NAIVE ? T : static_cast<long long>(ks.size());
+    const int S = dtype_bytes(dtype);
+    const bool tma_ok = tma_compatible(in, ld, dtype) && tma_compatible(out, ld, dtype);
+
+    if (c.kernel != SDFG_KERNEL_NAIVE && !tma_ok) {
+        // stage through two aligned pitched grids
+        const int ldp = (C + 31) / 32 * 32;
+        void *a = nullptr, *b = nullptr;
+        const size_t bytes = static_cast<size_t>(R) * ldp * S;
+        rc = scratch_alloc(&a, bytes, s);
+        if (rc == SDFG_OK) rc = scratch_alloc(&b, bytes, s);
+        void *fin = nullptr;
+        if (rc == SDFG_OK) rc = launch_copy2d(a, ldp, in, ld, R, C, dtype, s);
+        if (rc == SDFG_OK) rc = run_pass_sequence(a, b, a, ks, R, C, ldp, dtype, c, st, s, &fin);
+        if (rc == SDFG_OK) rc = launch_copy2d(out, ld, fin, ldp, R, C, dtype, s);
+        scratch_free(a, s);
+        scratch_free(b, s);
+        return rc;
+    }
+    if (in_disposable && in != out) {
+        void *fin = nullptr;
+        rc = run_pass_sequence(in, out, const_cast<void *>(in), ks, R, C, ld, dtype, c, st, s, &fin);
+        if (rc == SDFG_OK && fin != out) rc = launch_copy2d(out, ld, fin, ld, R, C, dtype, s);
+        return rc;
+    }
+    void *scr = nullptr;
+    rc = scratch_alloc(&scr, static_cast<size_t>(R) * ld * S, s);
+    if (rc != SDFG_OK) return rc;
+    void *first, *second;
+    if (in != out) {
+        first = (n_steps_total % 2 == 1) ? out : scr;
+        second = (first == out) ? scr : out;
+    } else {
+        first = scr;
+        second = out;
+    }
+    void *fin = nullptr;
+    rc = run_pass_sequence(in, first, second, ks, R, C, ld, dtype, c, st, s, &fin);
+    if (rc == SDFG_OK && fin != out) rc = launch_copy2d(out, ld, fin, ld, R, C, dtype, s);
+    scratch_free(scr, s);
+    return rc;
+}
+
+}  // namespace sdfg
+
+using namespace sdfg;
+
+extern "C" int sdfg_jacobi2d_cfg(const void *in, void *out, int rows, int cols, int ld, int T, int dtype,
+                                 const sdfg_config *cfg, void *stream) {
+    int rc = validate_grid(in, out, rows, cols, ld, T, dtype, "sdfg_jacobi2d");
+    if (rc != SDFG_OK) return rc;
+    return run_single(in, out, rows, cols, ld, T, dtype, cfg, false, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int sdfg_jacobi2d_ex(const void *in, void *out, int rows, int cols, int ld, int T, int dtype,
+                                void *stream) {
+    return sdfg_jacobi2d_cfg(in, out, rows, cols, ld, T, dtype, nullptr, stream);
+}
+
+extern "C" int sdfg_jacobi2d(const float *in, float *out, int rows, int cols, int T, void *stream) {
+    return sdfg_jacobi2d_cfg(in, out, rows, cols, cols, T, SDFG_F32, nullptr, stream);
+}
+
+namespace {
+// Device buffers reused by sdfg_jacobi2d_host between calls of the same size.
+struct HostCallCache {
+    std::mutex mu;
+    int device = -1;
+    size_t bytes = 0;
+    void *a = nullptr, *b = nullptr;
+};
+HostCallCache g_host_cache;
+}  // namespace
+
+extern "C" int sdfg_jacobi2d_host(const void *h_in, void *h_out, int rows, int cols, int T, int dtype,
+                                  void *stream) {
+    int rc = validate_grid(h_in, h_out, rows, cols, cols, T, dtype, "sdfg_jacobi2d_host");
+    if (rc != SDFG_OK) return rc;
+    if (rows == 0 || cols == 0) return SDFG_OK;
+    DeviceState *st = nullptr;
+    rc = current_device(&st);
+    if (rc != SDFG_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = static_cast<size_t>(rows) * cols * dtype_bytes(dtype);
+    std::lock_guard<std::mutex> lk(g_host_cache.mu);
+    if (g_host_cache.device != st->device || g_host_cache.bytes < bytes) {
+        if (g_host_cache.a) cudaFree(g_host_cache.a);
+        if (g_host_cache.b) cudaFree(g_host_cache.b);
+        g_host_cache.a = g_host_cache.b = nullptr;
+        g_host_cache.bytes = 0;
+        SDFG_CUDA(cudaMalloc(&g_host_cache.a, bytes));
+        SDFG_CUDA(cudaMalloc(&g_host_cache.b, bytes));
+        g_host_cache.bytes = bytes;
+        g_host_cache.device = st->device;
+    }
+    SDFG_CUDA(cudaMemcpyAsync(g_host_cache.a, h_in, bytes, cudaMemcpyHostToDevice, s));
+    rc = run_single(g_host_cache.a, g_host_cache.b, rows, cols, cols, T, dtype, nullptr, true, s);
+    if (rc != SDFG_OK) return rc;
+    SDFG_CUDA(cudaMemcpyAsync(h_out, g_host_cache.b, bytes, cudaMemcpyDeviceToHost, s));
+    SDFG_CUDA(cudaStreamSynchronize(s));
+    return SDFG_OK;
+}

@@ -1,0 +1,142 @@
+// Autotuner (paper Sec. 4: the performance engineer picks transformation
+// parameters; here the choice of fused depth k, warps per CTA and segment
+// height is measured instead of hand-picked).
+#include "autotune.h"
+
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "runtime.h"
+
+namespace sdfg {
+
+int run_single(const void *in, void *out, int R, int C, int ld, long long T, int dtype, const sdfg_config *cfg,
+               bool in_disposable, cudaStream_t s);
+
+namespace {
+using Key = std::tuple<int, int, int>;
+std::mutex g_mu;
+std::map<Key, sdfg_config> g_cache;
+bool g_loaded = false;
+
+int bucket(int n) {
+    int b = 0;
+    while ((1 << (b + 1)) <= n) ++b;
+    return b;
+}
+
+Key key_of(int rows, int cols, int dtype) { return Key(dtype, bucket(std::max(rows, 1)), bucket(std::max(cols, 1))); }
+
+void load_locked() {
+    if (g_loaded) return;
+    g_loaded = true;
+    const char *path = getenv("SDFG_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    int dt, br, bc, kern, k, seg, warps;
+    while (fscanf(f, "%d %d %d %d %d %d %d", &dt, &br, &bc, &kern, &k, &seg, &warps) == 7)
+        g_cache[Key(dt, br, bc)] = sdfg_config{kern, k, seg, warps};
+    fclose(f);
+}
+
+void save_locked() {
+    const char *path = getenv("SDFG_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "w");
+    if (!f) return;
+    for (auto &kv : g_cache)
+        fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                kv.second.kernel, kv.second.k, kv.second.seg_rows, kv.second.warps);
+    fclose(f);
+}
+}  // namespace
+
+bool autotune_lookup(int rows, int cols, int dtype, sdfg_config *out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_locked();
+    auto it = g_cache.find(key_of(rows, cols, dtype));
+    if (it == g_cache.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+void autotune_store(int rows, int cols, int dtype, const sdfg_config &c) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_locked();
+    g_cache[key_of(rows, cols, dtype)] = c;
+    save_locked();
+}
+
+}  // namespace sdfg
+
+using namespace sdfg;
+
+extern "C" int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *best, void *stream) {
+    if (!best || rows < 3 || cols < 3 || T < 1 || !dtype_valid(dtype))
+        return set_error(SDFG_ERR_INVAL, "sdfg_autotune: bad argument");
+    DeviceState *st = nullptr;
+    int rc = current_device(&st);
+    if (rc != SDFG_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int S = dtype_bytes(dtype);
+    const int ld = (cols + 31) / 32 * 32;
+    const size_t bytes = static_cast<size_t>(rows) * ld * S;
+    void *a = nullptr, *b = nullptr;
+    rc = scratch_alloc(&a, bytes, s);
+    if (rc == SDFG_OK) rc = scratch_alloc(&b, bytes, s);
+    if (rc != SDFG_OK) {
+        scratch_free(a, s);
+        return rc;
+    }
+    cudaMemsetAsync(a, 0, bytes, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // probe length: enough steps that each candidate runs a few passes
+    const long long Tp = std::min<long long>(T, 64);
+    const int ks[] = {1, 2, 4, 8};
+    const int warps_c[] = {4, 8};
+    const int segs_c[] = {0, 64, 256};
+    float best_ms = 1e30f;
+    sdfg_config winner = {SDFG_KERNEL_TEMPORAL, default_depth(dtype), 0, 8};
+    for (int k : ks) {
+        for (int w : warps_c) {
+            for (int sr : segs_c) {
+                sdfg_config c = {SDFG_KERNEL_TEMPORAL, k, sr, w};
+                // warm-up, then timed
+                rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);
+                if (rc != SDFG_OK) break;
+                cudaEventRecord(e0, s);
+                rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);
+                cudaEventRecord(e1, s);
+                if (rc != SDFG_OK) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = cuda_error(cudaGetLastError(), "autotune sync");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    winner = c;
+                }
+            }
+            if (rc != SDFG_OK) break;
+        }
+        if (rc != SDFG_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    scratch_free(a, s);
+    scratch_free(b, s);
+    if (rc != SDFG_OK) return rc;
+    autotune_store(rows, cols, dtype, winner);
+    *best = winner;
+    return SDFG_OK;
+}

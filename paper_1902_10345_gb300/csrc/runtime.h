@@ -1,0 +1,91 @@
+// Host-side runtime shared by every entry point: error reporting, per-device
+// state, tensor-map encoding, stream-ordered scratch, launch timing, and the
+// kernel launchers exported by kernels.cu.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/sdfg_jacobi.h"
+#include "geometry.h"
+
+namespace sdfg {
+
+// ---- errors ------------------------------------------------------------------
+int set_error(int code, const char *fmt, ...);    // records a thread-local message, returns code
+int cuda_error(cudaError_t e, const char *what);  // SDFG_ERR_CUDA (or NOMEM) with the CUDA message
+void clear_error();
+
+#define SDFG_CUDA(call)                                              \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return ::sdfg::cuda_error(e_, #call); \
+    } while (0)
+
+// ---- device state ------------------------------------------------------------
+struct DeviceState {
+    int device = -1;
+    int sm_count = 0;
+    int major = 0, minor = 0;
+    bool arch_ok = false;
+    int *d_err = nullptr;  // device error word (first failing code)
+};
+// State of the current device, created on first use.  Fails with
+// SDFG_ERR_UNSUPPORTED when the device is not an sm_103 part.
+int current_device(DeviceState **st);
+
+// ---- dtype -------------------------------------------------------------------
+inline bool dtype_valid(int dt) { return dt == SDFG_F32 || dt == SDFG_BF16 || dt == SDFG_F64; }
+inline int dtype_bytes(int dt) { return dt == SDFG_F64 ? 8 : (dt == SDFG_BF16 ? 2 : 4); }
+
+// ---- TMA ---------------------------------------------------------------------
+// 2-D tensor map over a rows x cols grid with pitch ld; box = box_cols x CHUNK_ROWS;
+// out-of-range elements read as zero.
+int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols, int ld, int box_cols);
+// True when a buffer can be read by TMA as laid out.
+inline bool tma_compatible(const void *p, int ld, int dtype) {
+    return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((static_cast<long long>(ld) * dtype_bytes(dtype)) % 16 == 0);
+}
+
+// ---- stream-ordered scratch --------------------------------------------------
+int scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+void scratch_free(void *p, cudaStream_t s);
+
+// ---- planning ----------------------------------------------------------------
+// Geometry of a grid for fused depth k (halo >= k).  seg_rows 0 = automatic,
+// aiming at `target_units` units.
+GridGeo plan_geometry(int rows, int cols, int ld, int dtype, int k, int seg_rows, long long target_units);
+// Pass depths for T steps at main depth k: k, k, ..., then the remainder in
+// powers of two (largest first).
+std::vector<int> plan_passes(long long T, int k);
+bool depth_supported(int k);
+int default_depth(int dtype);
+
+// ---- launch timing (sdfg_stats_*) ---------------------------------------------
+struct TimedLaunch {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int family = -1;
+    bool active() const { return family >= 0; }
+};
+enum Family { FAM_NAIVE = 0, FAM_TEMPORAL, FAM_PERSISTENT, FAM_REDUCE, FAM_COPY, FAM_COUNT };
+TimedLaunch stats_begin(int family, cudaStream_t s);
+void stats_end(TimedLaunch &t, cudaStream_t s);
+
+// ---- kernel launchers (kernels.cu) -------------------------------------------
+constexpr unsigned long long DEFAULT_TIMEOUT_NS = 2000000000ull;  // 2 s per wait
+
+int launch_naive_step(const void *A, void *B, int rows, int cols, int ld, int dtype, cudaStream_t s);
+int launch_temporal_pass(const CUtensorMap *tm_src, void *dst, const GridGeo &g, int dtype, int k, int warps,
+                         int res_flags, double2 *partials, int *err, unsigned long long timeout_ns,
+                         cudaStream_t s);
+// CTAs of `warps` warps resident per SM for the temporal kernel.
+int temporal_blocks_per_sm(int dtype, int k, int warps);
+size_t temporal_smem_bytes(int dtype, int warps);
+int launch_copy2d(void *dst, int ld_dst, const void *src, int ld_src, int rows, int cols, int dtype, cudaStream_t s);
+
+}  // namespace sdfg

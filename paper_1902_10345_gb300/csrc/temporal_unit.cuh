@@ -1,0 +1,313 @@
+// The temporal-blocked work unit: one warp advances one tile of the grid by
+// K timesteps in a single pass over HBM.
+//
+// Paper mapping (App. B transformations, applied by hand):
+//   MapTiling      -- the interior map is cut into strips of `wout` columns and
+//                     segments of `H` rows; one warp owns one (strip, segment);
+//   LocalStorage   -- rows of the tile are staged in shared memory by TMA;
+//   DoubleBuffering-- a ring of STAGES chunks: TMA fills chunk c+STAGES while
+//                     the warp computes on chunk c;
+//   Vectorization  -- each lane holds V consecutive columns (16-byte accesses
+//                     for FP32/FP64, 8-byte for BF16);
+//   StateFusion /
+//   MapToForLoop   -- K timestep-states are fused: the warp streams down its
+//                     column strip and keeps, for every fused level l < K, the
+//                     three most recent rows of level l in registers.  A new
+//                     level-0 row from shared memory lets level 0 produce one
+//                     row of level 1, which lets level 1 produce one row of
+//                     level 2, and so on; level K rows are final and go
+//                     straight to HBM.
+// West/east neighbours come from the adjacent lanes by warp shuffle; the
+// outermost lanes' values go stale by one column per level, so a strip
+// overlaps its neighbours by h >= K columns on each side (overlapped temporal
+// tiling); along rows a segment re-reads K rows above and below.
+//
+// The boundary ring is fixed (Dirichlet): a level never changes a point of
+// row 0, row R-1, column 0 or column C-1; rows/columns outside the grid come
+// from TMA's zero fill and only ever feed other outside points or the
+// boundary, whose value is copied, so they never reach a stored result.
+#pragma once
+
+#include "device_common.cuh"
+#include "geometry.h"
+
+namespace sdfg {
+
+// ---------------------------------------------------------------- one level --
+// o <- stencil(n, c, s) for the V columns of this lane; west of element 0 and
+// east of element V-1 come from the neighbouring lanes.
+template <int V, bool COLCHK>
+__device__ __forceinline__ void level_row(float (&o)[V], const float (&n)[V], const float (&c)[V],
+                                          const float (&s)[V], unsigned colmask) {
+    const float left = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
+    const float right = __shfl_down_sync(FULL_MASK, c[0], 1);
+    float we[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const float w = (e == 0) ? left : c[e - 1];
+        const float ea = (e == V - 1) ? right : c[e + 1];
+        we[e] = __fadd_rn(w, ea);
+    }
+#pragma unroll
+    for (int p = 0; p < V / 2; ++p) {
+        // packed FP32x2: (n+s), then (n+s)+(w+e), then c+(...), then *0.2
+        const float2 ns = __fadd2_rn(make_float2(n[2 * p], n[2 * p + 1]), make_float2(s[2 * p], s[2 * p + 1]));
+        const float2 t = __fadd2_rn(ns, make_float2(we[2 * p], we[2 * p + 1]));
+        const float2 u = __fadd2_rn(make_float2(c[2 * p], c[2 * p + 1]), t);
+        const float2 r = __fmul2_rn(make_float2(0.2f, 0.2f), u);
+        o[2 * p] = r.x;
+        o[2 * p + 1] = r.y;
+    }
+    if (COLCHK) {
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+            if ((colmask >> e) & 1u) o[e] = c[e];
+    }
+}
+
+template <int V, bool COLCHK>
+__device__ __forceinline__ void level_row(double (&o)[V], const double (&n)[V], const double (&c)[V],
+                                          const double (&s)[V], unsigned colmask) {
+    const double left = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
+    const double right = __shfl_down_sync(FULL_MASK, c[0], 1);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const double w = (e == 0) ? left : c[e - 1];
+        const double ea = (e == V - 1) ? right : c[e + 1];
+        o[e] = stencil_point(c[e], n[e], s[e], w, ea);
+    }
+    if (COLCHK) {
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+            if ((colmask >> e) & 1u) o[e] = c[e];
+    }
+}
+
+template <class ST, int V>
+__device__ __forceinline__ void storage_round(typename Store<ST>::CT (&o)[V]) {
+    if constexpr (sizeof(ST) == 2) {
+#pragma unroll
+        for (int e = 0; e < V; e += 2) {
+            const float2 f = __bfloat1622float2(__floats2bfloat162_rn(o[e], o[e + 1]));
+            o[e] = f.x;
+            o[e + 1] = f.y;
+        }
+    }
+}
+
+// A chunk wait ran out at step i: give the copies already in flight a short
+// bounded chance to land (so none writes shared memory after the warp has
+// left), then report failure.
+__device__ __noinline__ inline bool drain_after_timeout(uint64_t *bars, uint32_t base, int n_chunks, int i) {
+    const int c0 = i / CHUNK_ROWS;
+    for (int c = c0; c < n_chunks && c < c0 + STAGES; ++c) {
+        const uint32_t g = base + static_cast<uint32_t>(c);
+        mbar_wait_bounded(&bars[g % STAGES], (g / STAGES) & 1u, 1000000ull);
+    }
+    __syncwarp();
+    return false;
+}
+
+// ---------------------------------------------------------- the unit pipe --
+template <class ST, int V, int K, bool COLCHK>
+struct UnitPipe {
+    using CT = typename Store<ST>::CT;
+    static constexpr int W = 32 * V;
+    static constexpr uint32_t CHUNK_BYTES = CHUNK_ROWS * W * sizeof(ST);
+
+    CT b[K][3][V];  // level l, ring slot, column: rows r-l-2, r-l-1, r-l of level l
+
+    const void *tmap;
+    ST *dst;
+    int ld, R, C;
+    int X, y0, y1, rb, n_steps, n_chunks;
+    uint32_t base;
+    ST *ring;
+    uint64_t *bars;
+    int lane;
+    unsigned colmask, resmask;
+    bool own_lane, full_vec;
+    int res_flags;
+    CT g_ref, g_chk;  // group sums (at most CHUNK_ROWS rows of one lane)
+    double acc_ref, acc_chk;
+    unsigned long long timeout_ns;
+
+    __device__ __forceinline__ void issue(int c) {
+        const uint32_t slot = (base + static_cast<uint32_t>(c)) % STAGES;
+        mbar_arrive_expect_tx(&bars[slot], CHUNK_BYTES);
+        tma_load_2d(ring + slot * (CHUNK_ROWS * W), tmap, X, rb + c * CHUNK_ROWS, &bars[slot]);
+    }
+
+    __device__ __forceinline__ void accumulate(CT &g, const CT (&o)[V], const CT (&c)[V]) {
+        CT sum = CT(0);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            if ((resmask >> e) & 1u) {
+                const CT d = o[e] - c[e];
+                sum = fma(d, d, sum);
+            }
+        }
+        g = g + sum;
+    }
+
+    __device__ __forceinline__ void store_row(int row, const CT (&o)[V]) {
+        ST *p = dst + static_cast<size_t>(row) * ld + (X + lane * V);
+        if (full_vec) {
+            VecIO<ST, V>::store(p, o);
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (X + lane * V + e < C) p[e] = from_ct<ST>(o[e]);
+        }
+    }
+
+    template <int PH>
+    __device__ __forceinline__ bool step(int i) {
+        constexpr int SN = (PH + 1) % 3;  // slot of the north row
+        constexpr int SC = (PH + 2) % 3;  // slot of the centre row
+        constexpr int SS = PH;            // slot of the south (newest) row
+        const int c = i / CHUNK_ROWS;
+        const int rr = i - c * CHUNK_ROWS;
+        const uint32_t g = base + static_cast<uint32_t>(c);
+        const uint32_t slot = g % STAGES;
+        if (rr == 0) {
+            // every lane waits (acquiring the TMA-written rows); the outcome is
+            // made warp-uniform so no lane is left behind in a shuffle
+            const bool ok = mbar_wait_bounded(&bars[slot], (g / STAGES) & 1u, timeout_ns);
+            if (!__all_sync(FULL_MASK, ok)) return false;
+        }
+        {
+            CT tmp[V];
+            VecIO<ST, V>::load(tmp, ring + (slot * CHUNK_ROWS + rr) * W + lane * V);
+#pragma unroll
+            for (int e = 0; e < V; ++e) b[0][SS][e] = tmp[e];
+        }
+        const int r = rb + i;
+        const bool rowchk = (r <= K) || (r >= R);
+#pragma unroll
+        for (int l = 0; l < K; ++l) {
+            CT o[V];
+            level_row<V, COLCHK>(o, b[l][SN], b[l][SC], b[l][SS], colmask);
+            if (rowchk) {
+                const int rc = r - l - 1;  // row index of this level's centre
+                if (rc <= 0 || rc >= R - 1) {
+#pragma unroll
+                    for (int e = 0; e < V; ++e) o[e] = b[l][SC][e];
+                }
+            }
+            storage_round<ST, V>(o);
+            if (l == 0 && (res_flags & 1)) {
+                const int row = r - 1;
+                if (row >= y0 && row < y1) accumulate(g_ref, o, b[0][SC]);
+            }
+            if (l == K - 1) {
+                const int row = r - K;
+                if (row >= y0 && row < y1) {
+                    if (res_flags & 2) accumulate(g_chk, o, b[l][SC]);
+                    if (own_lane) store_row(row, o);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) b[l + 1][SS][e] = o[e];
+            }
+        }
+        if (rr == CHUNK_ROWS - 1 || i == n_steps - 1) {
+            // every lane has consumed chunk c: recycle its slot
+            __syncwarp();
+            if (lane == 0 && c + STAGES < n_chunks) issue(c + STAGES);
+            if (res_flags) {
+                acc_ref += static_cast<double>(g_ref);
+                acc_chk += static_cast<double>(g_chk);
+                g_ref = CT(0);
+                g_chk = CT(0);
+            }
+        }
+        return true;
+    }
+
+    __device__ __forceinline__ bool run() {
+#pragma unroll
+        for (int l = 0; l < K; ++l)
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+#pragma unroll
+                for (int e = 0; e < V; ++e) b[l][s][e] = CT(0);
+        g_ref = g_chk = CT(0);
+        acc_ref = acc_chk = 0.0;
+        if (lane == 0) {
+            const int first = n_chunks < STAGES ? n_chunks : STAGES;
+            for (int c = 0; c < first; ++c) issue(c);
+        }
+        int i = 0;
+        for (; i + 2 < n_steps; i += 3) {
+            if (!step<0>(i)) return drain_after_timeout(bars, base, n_chunks, i);
+            if (!step<1>(i + 1)) return drain_after_timeout(bars, base, n_chunks, i + 1);
+            if (!step<2>(i + 2)) return drain_after_timeout(bars, base, n_chunks, i + 2);
+        }
+        if (i < n_steps && !step<0>(i)) return drain_after_timeout(bars, base, n_chunks, i);
+        if (i + 1 < n_steps && !step<1>(i + 1)) return drain_after_timeout(bars, base, n_chunks, i + 1);
+        return true;
+    }
+};
+
+// Process unit (strip, seg) of grid `g`: read through tensor map `tmap`
+// (source buffer), write `dst`.  res_flags bit 0: accumulate the squared
+// level-1 update (the first step of a solve), bit 1: the squared level-K
+// update (a check step).  Returns false if a TMA wait ran out.
+template <class ST, int V, int K>
+__device__ __forceinline__ bool run_unit(const void *tmap, ST *dst, const GridGeo &g, int strip, int seg, ST *ring,
+                                         uint64_t *bars, uint32_t &chunk_ctr, int res_flags, double2 *partial,
+                                         unsigned long long timeout_ns) {
+    constexpr int W = 32 * V;
+    const int lane = threadIdx.x & 31;
+    const int X = strip * g.wout - g.h;
+    const int y0 = seg * g.H;
+    const int y1 = min(y0 + g.H, g.R);
+    const int rb = max(0, y0 - K);
+    const int n_steps = y1 + K - rb;
+    const int n_chunks = (n_steps + CHUNK_ROWS - 1) / CHUNK_ROWS;
+    const int gc0 = X + lane * V;
+    const int hl = g.h / V;
+
+    unsigned colmask = 0, resmask = 0;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int gc = gc0 + e;
+        if (gc <= 0 || gc >= g.C - 1) colmask |= 1u << e;
+        if (gc >= 1 && gc <= g.C - 2) resmask |= 1u << e;
+    }
+    const bool own_lane = lane >= hl && lane < 32 - hl && gc0 < g.C;
+    if (!own_lane) resmask = 0;
+    const bool full_vec = gc0 + V <= g.C;
+    const bool colchk = (X <= 0) || (X + W > g.C - 1);
+
+    bool ok;
+    double ar = 0.0, ac = 0.0;
+#define SDFG_RUN_PIPE(CHK)                                                                              \
+    {                                                                                                   \
+        UnitPipe<ST, V, K, CHK> p;                                                                      \
+        p.tmap = tmap; p.dst = dst; p.ld = g.ld; p.R = g.R; p.C = g.C;                                  \
+        p.X = X; p.y0 = y0; p.y1 = y1; p.rb = rb; p.n_steps = n_steps; p.n_chunks = n_chunks;           \
+        p.base = chunk_ctr; p.ring = ring; p.bars = bars; p.lane = lane;                                \
+        p.colmask = colmask; p.resmask = resmask; p.own_lane = own_lane; p.full_vec = full_vec;         \
+        p.res_flags = res_flags; p.timeout_ns = timeout_ns;                                             \
+        ok = p.run();                                                                                   \
+        ar = p.acc_ref; ac = p.acc_chk;                                                                 \
+    }
+    if (colchk) SDFG_RUN_PIPE(true) else SDFG_RUN_PIPE(false)
+#undef SDFG_RUN_PIPE
+    chunk_ctr += static_cast<uint32_t>(n_chunks);
+
+    if (res_flags && partial) {
+        // fixed-order butterfly; lane 0's value is used
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            ar += __shfl_xor_sync(FULL_MASK, ar, off);
+            ac += __shfl_xor_sync(FULL_MASK, ac, off);
+        }
+        if (lane == 0) *partial = make_double2(ar, ac);
+    }
+    return ok;
+}
+
+}  // namespace sdfg

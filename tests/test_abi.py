@@ -1,0 +1,95 @@
+"""The C-ABI library loads on a machine without a GPU, exports every function
+the headers declare, rejects bad arguments on the host before touching the
+GPU, and plans work decompositions that cover the grid."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1902_10345_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"\b(sdfg_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding mirrors each of them
+    assert set(names) <= set(binding._PROTOS), set(names) - set(binding._PROTOS)
+
+
+def test_version(lib):
+    assert binding.sdfg_version() >= 100
+
+
+@pytest.mark.parametrize("args", [
+    (1, 0, 8, 8, 8, 5, 7),      # bad dtype
+    (1, 0, -1, 8, 8, 5, 0),     # negative rows
+    (1, 0, 8, 8, 4, 5, 0),      # ld < cols
+    (1, 0, 8, 8, 8, -3, 0),     # negative T
+    (0, 0, 8, 8, 8, 5, 0),      # null pointers
+])
+def test_host_validation(lib, args):
+    inp, out, R, C, ld, T, dt = args
+    pi = 4096 if inp else 0
+    po = 1 << 20 if args[1] == 0 and inp else 0
+    rc = binding.sdfg_jacobi2d_ex(pi, po, R, C, ld, T, dt, 0)
+    assert rc == binding.SDFG_ERR_INVAL
+    assert binding.last_error()
+
+
+def test_overlap_rejected(lib):
+    # out starts inside in's span: neither equal nor disjoint
+    rc = binding.sdfg_jacobi2d_ex(1 << 20, (1 << 20) + 64, 8, 8, 8, 3, binding.SDFG_F32, 0)
+    assert rc == binding.SDFG_ERR_INVAL
+    assert "overlap" in binding.last_error()
+
+
+def test_bad_config_rejected(lib):
+    cfg = binding.config(kernel=binding.SDFG_KERNEL_TEMPORAL, k=3)
+    rc = binding.sdfg_jacobi2d_cfg(1 << 20, 1 << 24, 8, 8, 8, 3, binding.SDFG_F32, cfg, 0)
+    # k=3 is rejected when the config is resolved (after the device check on a
+    # GPU machine; here the device check itself fails first)
+    assert rc < 0
+
+
+@pytest.mark.parametrize("dtype", [binding.SDFG_F32, binding.SDFG_BF16, binding.SDFG_F64])
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+@pytest.mark.parametrize("shape", [(3, 3), (100, 77), (8192, 8192), (257, 1000)])
+def test_plan_geometry_covers_grid(lib, dtype, k, shape):
+    R, C = shape
+    g = binding.sdfg_plan_geometry(R, C, dtype, k, 0)
+    elem = {binding.SDFG_F32: 4, binding.SDFG_BF16: 2, binding.SDFG_F64: 8}[dtype]
+    V = 2 if elem == 8 else 4
+    assert g["warp_cols"] == 32 * V
+    assert g["halo_cols"] >= k and g["halo_cols"] % V == 0
+    assert (g["halo_cols"] * elem) % 16 == 0             # TMA x coordinate alignment
+    assert g["out_cols_per_strip"] == g["warp_cols"] - 2 * g["halo_cols"]
+    assert g["out_cols_per_strip"] >= g["halo_cols"]      # only adjacent strips share halos
+    assert g["n_strips"] * g["out_cols_per_strip"] >= C
+    assert (g["n_strips"] - 1) * g["out_cols_per_strip"] < C
+    assert g["n_segs"] * g["seg_rows"] >= R and (g["n_segs"] - 1) * g["seg_rows"] < R
+
+
+def test_plan_geometry_rejects_bad_depth(lib):
+    with pytest.raises(binding.SdfgError):
+        binding.sdfg_plan_geometry(64, 64, binding.SDFG_F32, 3, 0)

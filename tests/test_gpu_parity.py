@@ -1,0 +1,225 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Tolerances (max-abs against the FP64 oracle run on exactly the values the GPU
+received): FP32 storage 1e-4, BF16 storage 2e-2, FP64 1e-12 (and bitwise, the
+order of operations being the same).  All kernels and fused depths evaluate
+every update in the same order, so their results must agree bit for bit.
+
+Full-size cases (8192^2, T=1000) are checked on light-cone windows: the
+oracle runs on a crop that extends T+1 cells past each window, which fixes the
+window's values exactly; plus transpose symmetry and the maximum principle,
+which hold at any size.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1902_10345_gb300 import binding, build, inputs
+
+pytestmark = pytest.mark.gpu
+
+F32, BF16, F64 = binding.SDFG_F32, binding.SDFG_BF16, binding.SDFG_F64
+TDT = {F32: torch.float32, BF16: torch.bfloat16, F64: torch.float64}
+TOL = {F32: 1e-4, BF16: 2e-2, F64: 1e-12}
+NAIVE = binding.SDFG_KERNEL_NAIVE
+TEMPORAL = binding.SDFG_KERNEL_TEMPORAL
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    L = binding.lib()
+    binding.sdfg_device_error(True)
+    return L
+
+
+def dev(grid64, dt, ld=None):
+    t = torch.from_numpy(np.ascontiguousarray(grid64)).to(TDT[dt])
+    R, C = t.shape
+    if ld is None or ld == C:
+        return t.cuda()
+    buf = torch.zeros((R, ld), dtype=TDT[dt], device="cuda")
+    buf[:, :C] = t.cuda()
+    return buf[:, :C]
+
+
+def host64(t):
+    return t.double().cpu().numpy()
+
+
+def run(inp, T, cfg=None, out=None, inplace=False):
+    if inplace:
+        out = inp
+    elif out is None:
+        out = torch.empty_like(inp) if inp.is_contiguous() else dev(np.zeros(inp.shape), binding.dtype_code(inp),
+                                                                     inp.stride(0))
+    binding.jacobi2d(inp, out, T, cfg)
+    torch.cuda.synchronize()
+    assert binding.sdfg_device_error(True) == 0
+    return out
+
+
+def cfg(kernel, k=0, seg_rows=0, warps=0):
+    return binding.config(kernel=kernel, k=k, seg_rows=seg_rows, warps=warps)
+
+
+ALL_CFGS = [cfg(NAIVE)] + [cfg(TEMPORAL, k) for k in (1, 2, 4, 8)] + [cfg(TEMPORAL, 8, seg_rows=16, warps=4),
+                                                                     cfg(TEMPORAL, 4, seg_rows=24, warps=2)]
+
+
+@pytest.mark.parametrize("shape", [(3, 3), (4, 4), (5, 7), (9, 130), (17, 33), (64, 64), (129, 131), (200, 515),
+                                   (40, 1100)])
+@pytest.mark.parametrize("T", [1, 5, 16, 37])
+def test_f32_matches_oracle_all_kernels(shape, T):
+    R, C = shape
+    g = inputs.uniform_grid(R, C, seed=R * 1000 + C)
+    x = dev(g, F32)
+    want = oracle.jacobi2d(host64(x), T, threads=0)
+    results = []
+    for c in ALL_CFGS:
+        y = host64(run(x, T, c))
+        err = np.abs(y - want).max()
+        assert err <= TOL[F32], (shape, T, c.kernel, c.k, err)
+        results.append(y)
+    for y in results[1:]:
+        assert np.array_equal(y, results[0]), "kernels disagree bitwise"
+    # input untouched
+    assert np.array_equal(host64(x), g.astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("dt", [BF16, F64])
+@pytest.mark.parametrize("shape,T", [((33, 70), 9), ((130, 257), 21), ((300, 1000), 40)])
+def test_other_dtypes_match_oracle(dt, shape, T):
+    R, C = shape
+    g = inputs.sinusoid_field(max(R, C), seed=3)[:R, :C]
+    x = dev(g, dt)
+    want = oracle.jacobi2d(host64(x), T, threads=0)
+    outs = []
+    for c in [cfg(NAIVE), cfg(TEMPORAL, 1), cfg(TEMPORAL, 2), cfg(TEMPORAL, 4), cfg(TEMPORAL, 8)]:
+        y = host64(run(x, T, c))
+        err = np.abs(y - want).max()
+        assert err <= TOL[dt], (dt, shape, T, c.k, err)
+        outs.append(y)
+    for y in outs[1:]:
+        assert np.array_equal(y, outs[0])
+    if dt == F64:
+        assert np.array_equal(outs[0], want), "FP64 path should equal the oracle bit for bit"
+
+
+def test_f64_256_grid_T100_bitwise():
+    g = inputs.uniform_grid(256, 256, seed=0)
+    x = dev(g, F64)
+    want = oracle.jacobi2d(g, 100)
+    y = host64(run(x, 100))
+    assert np.abs(y - want).max() <= TOL[F64]
+    assert np.array_equal(y, want)
+
+
+def test_f32_256_grid_T100():
+    g = inputs.uniform_grid(256, 256, seed=0)
+    x = dev(g, F32)
+    want = oracle.jacobi2d(host64(x), 100)
+    assert np.abs(host64(run(x, 100)) - want).max() <= TOL[F32]
+
+
+@pytest.mark.parametrize("T", [6, 8, 9, 16, 17])
+def test_in_place(T):
+    g = inputs.uniform_grid(70, 90, seed=T)
+    want = oracle.jacobi2d(g.astype(np.float32).astype(np.float64), T)
+    for c in [cfg(TEMPORAL, 8), cfg(TEMPORAL, 4), cfg(NAIVE)]:
+        x = dev(g, F32)
+        run(x, T, c, inplace=True)
+        assert np.abs(host64(x) - want).max() <= TOL[F32]
+
+
+@pytest.mark.parametrize("ld_extra", [4, 12, 3, 1])
+def test_pitched_and_unaligned_layouts(ld_extra):
+    # ld*4 % 16 == 0 for extra 4/12 (TMA reads the caller's buffers directly);
+    # 3 and 1 need the staged path
+    R, C, T = 50, 68, 13
+    g = inputs.uniform_grid(R, C, seed=ld_extra)
+    x = dev(g, F32, ld=C + ld_extra)
+    y = dev(np.zeros((R, C)), F32, ld=C + ld_extra)
+    run(x, T, cfg(TEMPORAL, 4), out=y)
+    want = oracle.jacobi2d(host64(x), T)
+    assert np.abs(host64(y) - want).max() <= TOL[F32]
+
+
+@pytest.mark.parametrize("cols", [61, 127, 129, 8190 // 64])
+def test_ragged_widths(cols):
+    R, T = 45, 11
+    g = inputs.uniform_grid(R, cols, seed=cols)
+    x = dev(g, F32)
+    want = oracle.jacobi2d(host64(x), T)
+    for c in [cfg(TEMPORAL, 8), cfg(TEMPORAL, 2)]:
+        assert np.abs(host64(run(x, T, c)) - want).max() <= TOL[F32]
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 17), (2, 9), (9, 2), (2, 2), (3, 40)])
+def test_degenerate_shapes(shape):
+    g = inputs.uniform_grid(*shape, seed=1)
+    x = dev(g, F32)
+    want = oracle.jacobi2d(host64(x), 7)
+    assert np.array_equal(host64(run(x, 7)), want)
+
+
+def test_T0_and_empty():
+    g = inputs.uniform_grid(20, 30, seed=2)
+    x = dev(g, F32)
+    assert np.array_equal(host64(run(x, 0)), host64(x))
+    e = torch.empty((0, 5), device="cuda")
+    binding.check(binding.sdfg_jacobi2d(e.data_ptr(), e.data_ptr(), 0, 5, 3, 0))
+
+
+def test_raw_entry_point_and_host_call():
+    R, C, T = 96, 160, 24
+    g = inputs.uniform_grid(R, C, seed=11)
+    x = dev(g, F32)
+    y = torch.empty_like(x)
+    binding.check(binding.sdfg_jacobi2d(x.data_ptr(), y.data_ptr(), R, C, T, torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    want = oracle.jacobi2d(host64(x), T)
+    assert np.abs(host64(y) - want).max() <= TOL[F32]
+    hi = x.cpu().pin_memory()
+    ho = torch.empty_like(hi).pin_memory()
+    binding.check(binding.sdfg_jacobi2d_host(hi.data_ptr(), ho.data_ptr(), R, C, T, F32, 0))
+    assert np.array_equal(ho.double().numpy(), host64(y))
+
+
+def test_full_size_8192_T1000_windows_and_properties():
+    """The bench workload: 8192^2 FP32, T=1000, in the bench's launch config."""
+    R = C = 8192
+    T = 1000
+    g = inputs.uniform_grid(R, C, seed=0)
+    x = dev(g, F32)
+    y = run(x, T)
+    yh = y.cpu().numpy()
+    xh = x.cpu().numpy().astype(np.float64)
+    for (r0, c0) in [(0, 0), (0, C - 24), (R - 24, 0), (R - 24, C - 24), (4000, 4100), (0, 3000), (5000, C - 24)]:
+        w = oracle.jacobi2d_window(xh, T, r0, r0 + 24, c0, c0 + 24, threads=0)
+        err = np.abs(yh[r0:r0 + 24, c0:c0 + 24].astype(np.float64) - w).max()
+        assert err <= TOL[F32], (r0, c0, err)
+    # discrete maximum principle
+    assert yh.min() >= xh.min() - 1e-6 and yh.max() <= xh.max() + 1e-6
+    # transpose symmetry, bit for bit
+    yt = run(x.t().contiguous(), T)
+    assert torch.equal(yt.t(), y)
+    # boundary ring untouched
+    assert torch.equal(y[0], x[0]) and torch.equal(y[-1], x[-1])
+    assert torch.equal(y[:, 0], x[:, 0]) and torch.equal(y[:, -1], x[:, -1])
+
+
+def test_paper_workload_eigenmode_2048_T1024():
+    """Zero boundary, 2048^2, T=1024 (the paper's Jacobi workload), on a
+    closed-form eigenmode: the amplitude after T steps is lambda^T."""
+    import math
+    R = C = 2048
+    T = 1024
+    g = inputs.eigenmode(R, C, 3, 5)
+    lam = 0.2 + 0.4 * (math.cos(3 * math.pi / (R - 1)) + math.cos(5 * math.pi / (C - 1)))
+    x = dev(g, F32)
+    y = host64(run(x, T))
+    want = (lam ** T) * host64(x)
+    assert np.abs(y - want).max() <= TOL[F32]
