@@ -199,6 +199,16 @@ int sdfg_device_error(int clear);
 /* Thread-local description of the last failure on this thread. */
 const char *sdfg_last_error(void);
 
+/*
+ * Test hooks for the failure paths (no GPU fault is involved):
+ *   hook 1, value 0/1: persistent launches created afterwards make their first
+ *           work item wait on a flag that nothing sets, so the bounded wait
+ *           runs out and the launch reports SDFG_ERR_TIMEOUT;
+ *   hook 2, value ns: limit of every bounded device wait in persistent
+ *           launches created afterwards (0 = default, 2 s).
+ */
+int sdfg_test_hook(int hook, long long value);
+
 /* Library version (major*10000 + minor*100 + patch). */
 int sdfg_version(void);
 

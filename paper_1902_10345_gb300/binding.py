@@ -69,6 +69,7 @@ _PROTOS = {
     "sdfg_device_error": (_I, [_I]),
     "sdfg_last_error": (ctypes.c_char_p, []),
     "sdfg_version": (_I, []),
+    "sdfg_test_hook": (_I, [_I, ctypes.c_longlong]),
     "sdfg_plan_geometry": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_int)]),
 }
 
@@ -161,6 +162,10 @@ def sdfg_stats_get(name: str):
 
 def sdfg_device_error(clear: bool = True) -> int:
     return lib().sdfg_device_error(1 if clear else 0)
+
+
+def sdfg_test_hook(hook: int, value: int) -> int:
+    return lib().sdfg_test_hook(hook, value)
 
 
 def sdfg_version() -> int:

@@ -24,6 +24,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-Xptxas", "-warn-spills"]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function"]
+# developer knob: extra nvcc flags (e.g. -DSDFG_TP_MAXT=128 -DSDFG_TP_MINB=4)
+NVCC_FLAGS += os.environ.get("SDFG_NVCC_EXTRA", "").split()
 
 
 def cuda_home() -> str:

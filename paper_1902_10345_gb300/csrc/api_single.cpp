@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "autotune.h"
+#include "launchset.h"
 #include "runtime.h"
 
 namespace sdfg {
@@ -46,7 +47,7 @@ int resolve_config(const sdfg_config *cfg, int R, int C, int dtype, sdfg_config 
     const bool have = autotune_lookup(R, C, dtype, &tuned);
     if (c.kernel == SDFG_KERNEL_AUTO) c.kernel = have ? tuned.kernel : SDFG_KERNEL_TEMPORAL;
     if (c.k == 0) c.k = have && tuned.k ? tuned.k : default_depth(dtype);
-    if (c.warps == 0) c.warps = have && tuned.warps ? tuned.warps : 8;
+    if (c.warps == 0) c.warps = have && tuned.warps ? tuned.warps : 4;
     if (c.seg_rows == 0 && have) c.seg_rows = tuned.seg_rows;
     *out = c;
     return SDFG_OK;
@@ -94,6 +95,87 @@ static int run_pass_sequence(const void *src0, void *first, void *second, const 
     return SDFG_OK;
 }
 
+int enqueue_persistent(LaunchSet &ls, DeviceState *st, cudaStream_t s);
+
+// ---- single grid through the persistent kernel ------------------------------
+// Uploaded launch plans are kept for repeated calls with the same arguments
+// (pointers, shape, T, configuration): a repeat only resets the plan's
+// counters and launches.  At most kSingleCacheSize plans (and their scratch
+// grids) are kept per process.
+namespace {
+struct SingleKey {
+    const void *in;
+    void *out;
+    int R, C, ld, dtype, k, warps, seg_rows, device;
+    long long T;
+    bool operator==(const SingleKey &o) const {
+        return in == o.in && out == o.out && R == o.R && C == o.C && ld == o.ld && dtype == o.dtype && k == o.k &&
+               warps == o.warps && seg_rows == o.seg_rows && device == o.device && T == o.T;
+    }
+};
+struct SingleEntry {
+    SingleKey key;
+    LaunchSet ls;
+    void *scratch = nullptr;
+    int last = 0;  // buffer holding the result
+    unsigned long long stamp = 0;
+};
+constexpr size_t kSingleCacheSize = 8;
+std::mutex g_single_mu;
+std::vector<SingleEntry *> g_single;
+unsigned long long g_single_clock = 0;
+}  // namespace
+
+static int run_single_persistent(const void *in, void *out, int R, int C, int ld, long long T, int dtype,
+                                 const sdfg_config &c, DeviceState *st, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_single_mu);
+    const SingleKey key{in, out, R, C, ld, dtype, c.k, c.warps, c.seg_rows, st->device, T};
+    SingleEntry *e = nullptr;
+    for (SingleEntry *x : g_single)
+        if (x->key == key) e = x;
+    if (!e) {
+        if (g_single.size() >= kSingleCacheSize) {
+            auto it = std::min_element(g_single.begin(), g_single.end(),
+                                       [](SingleEntry *a, SingleEntry *b) { return a->stamp < b->stamp; });
+            (*it)->ls.release(s);
+            scratch_free((*it)->scratch, s);
+            delete *it;
+            g_single.erase(it);
+        }
+        e = new SingleEntry();
+        e->key = key;
+        int rc = scratch_alloc(&e->scratch, static_cast<size_t>(R) * ld * dtype_bytes(dtype), s);
+        GridRun r;
+        r.buf[0] = out;
+        r.buf[1] = e->scratch;
+        r.buf[2] = in == out ? nullptr : const_cast<void *>(in);
+        r.cur = in == out ? 0 : 2;
+        r.ld = ld;
+        r.R = R;
+        r.C = C;
+        r.steps = static_cast<int>(T);
+        r.T_cap = static_cast<int>(T);
+        r.seg_rows = c.seg_rows;
+        e->ls.dtype = dtype;
+        e->ls.k = c.k;
+        e->ls.warps = c.warps;
+        if (rc == SDFG_OK) rc = e->ls.build(std::vector<GridRun>(1, r));
+        if (rc == SDFG_OK) rc = e->ls.upload(s);
+        if (rc != SDFG_OK) {
+            e->ls.release(s);
+            scratch_free(e->scratch, s);
+            delete e;
+            return rc;
+        }
+        e->last = e->ls.last_dst[0];
+        g_single.push_back(e);
+    }
+    e->stamp = ++g_single_clock;
+    int rc = enqueue_persistent(e->ls, st, s);
+    if (rc == SDFG_OK && e->last != 0) rc = launch_copy2d(out, ld, e->scratch, ld, R, C, dtype, s);
+    return rc;
+}
+
 // Core single-grid run.  in_disposable: `in` may be overwritten (it then
 // serves as the scratch grid).
 int run_single(const void *in, void *out, int R, int C, int ld, long long T, int dtype, const sdfg_config *cfg,
@@ -111,6 +193,13 @@ int run_single(const void *in, void *out, int R, int C, int ld, long long T, int
     const long long n_steps_total = c.kernel == SDFG_KERNEL_NAIVE ? T : static_cast<long long>(ks.size());
     const int S = dtype_bytes(dtype);
     const bool tma_ok = tma_compatible(in, ld, dtype) && tma_compatible(out, ld, dtype);
+    if (c.kernel == SDFG_KERNEL_PERSISTENT && tma_ok && !in_disposable) {
+        sdfg_config pc = c;
+        if (pc.seg_rows == 0) pc.seg_rows = 128;
+        if (pc.warps > 4) pc.warps = 4;
+        return run_single_persistent(in, out, R, C, ld, T, dtype, pc, st, s);
+    }
+    if (c.kernel == SDFG_KERNEL_PERSISTENT) c.kernel = SDFG_KERNEL_TEMPORAL;
 
     if (c.kernel != SDFG_KERNEL_NAIVE && !tma_ok) {
         // stage through two aligned pitched grids

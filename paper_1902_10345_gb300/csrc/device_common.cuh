@@ -132,6 +132,19 @@ template <> struct VecIO<float, 4> {
     }
 };
 
+template <> struct VecIO<float, 8> {
+    __device__ __forceinline__ static void load(float (&d)[8], const float *p) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[0];
+        const float4 b = reinterpret_cast<const float4 *>(p)[1];
+        d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
+        d[4] = b.x; d[5] = b.y; d[6] = b.z; d[7] = b.w;
+    }
+    __device__ __forceinline__ static void store(float *p, const float (&s)[8]) {
+        reinterpret_cast<float4 *>(p)[0] = make_float4(s[0], s[1], s[2], s[3]);
+        reinterpret_cast<float4 *>(p)[1] = make_float4(s[4], s[5], s[6], s[7]);
+    }
+};
+
 template <> struct VecIO<__nv_bfloat16, 4> {
     __device__ __forceinline__ static void load(float (&d)[4], const __nv_bfloat16 *p) {
         uint2 u = *reinterpret_cast<const uint2 *>(p);
@@ -160,6 +173,42 @@ template <> struct VecIO<double, 2> {
         *reinterpret_cast<double2 *>(p) = make_double2(s[0], s[1]);
     }
 };
+
+// Predicated vector stores (one instruction, no branch): write V elements at
+// p when `pred` is non-zero.
+__device__ __forceinline__ void store_pred(float *p, const float (&s)[4], int pred) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t"
+        "@q st.global.v4.f32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(p),
+        "f"(s[0]), "f"(s[1]), "f"(s[2]), "f"(s[3]), "r"(pred)
+        : "memory");
+}
+__device__ __forceinline__ void store_pred(float *p, const float (&s)[8], int pred) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %9, 0;\n\t"
+        "@q st.global.v4.f32 [%0], {%1, %2, %3, %4};\n\t"
+        "@q st.global.v4.f32 [%0+16], {%5, %6, %7, %8};\n\t}" ::"l"(p),
+        "f"(s[0]), "f"(s[1]), "f"(s[2]), "f"(s[3]), "f"(s[4]), "f"(s[5]), "f"(s[6]), "f"(s[7]), "r"(pred)
+        : "memory");
+}
+__device__ __forceinline__ void store_pred(__nv_bfloat16 *p, const float (&s)[4], int pred) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(s[0], s[1]);
+    __nv_bfloat162 b = __floats2bfloat162_rn(s[2], s[3]);
+    const uint32_t ua = *reinterpret_cast<uint32_t *>(&a);
+    const uint32_t ub = *reinterpret_cast<uint32_t *>(&b);
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t"
+        "@q st.global.v2.b32 [%0], {%1, %2};\n\t}" ::"l"(p),
+        "r"(ua), "r"(ub), "r"(pred)
+        : "memory");
+}
+__device__ __forceinline__ void store_pred(double *p, const double (&s)[2], int pred) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t"
+        "@q st.global.v2.f64 [%0], {%1, %2};\n\t}" ::"l"(p),
+        "d"(s[0]), "d"(s[1]), "r"(pred)
+        : "memory");
+}
 
 template <class ST> __device__ __forceinline__ typename Store<ST>::CT to_ct(ST v);
 template <> __device__ __forceinline__ float to_ct<float>(float v) { return v; }

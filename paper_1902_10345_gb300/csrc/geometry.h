@@ -3,8 +3,8 @@
 
 namespace sdfg {
 
-constexpr int CHUNK_ROWS = 8;  // rows per TMA box
-constexpr int STAGES = 3;      // TMA ring depth per warp
+constexpr int CHUNK_ROWS = 6;  // rows per TMA box (a multiple of the 3-row register rotation)
+constexpr int STAGES = 4;      // TMA ring depth per warp
 constexpr int MAX_WARPS = 16;  // warps per CTA upper bound
 
 // Codes a kernel writes to the per-device error word (first writer wins).
@@ -23,8 +23,12 @@ struct GridGeo {
     int n_segs;     // ceil(R / H)
 };
 
-// Columns per lane for a storage size in bytes: FP32 4, BF16 4, FP64 2.
-inline int lane_cols(int elem_bytes) { return elem_bytes == 8 ? 2 : 4; }
+#ifndef SDFG_F32_V
+#define SDFG_F32_V 4  // FP32 columns per lane (4 or 8)
+#endif
+
+// Columns per lane for a storage size in bytes: FP32 SDFG_F32_V, BF16 4, FP64 2.
+inline int lane_cols(int elem_bytes) { return elem_bytes == 8 ? 2 : (elem_bytes == 4 ? SDFG_F32_V : 4); }
 
 // TMA x alignment in elements (16 bytes).
 inline int tma_xalign(int elem_bytes) { return 16 / elem_bytes; }

@@ -68,8 +68,15 @@ int launch_copy2d(void *dst, int ldd, const void *src, int lds, int R, int C, in
 // One launch = one pass of K fused timesteps over the whole grid; each warp
 // owns one (strip, segment) unit, strips fastest so that neighbouring warps
 // share halo columns through L2.
+#ifndef SDFG_TP_MAXT
+#define SDFG_TP_MAXT 128  // threads per CTA the temporal kernel is compiled for
+#endif
+#ifndef SDFG_TP_MINB
+#define SDFG_TP_MINB 3    // CTAs per SM the register allocation must allow
+#endif
+
 template <class ST, int V, int K>
-__global__ void __launch_bounds__(256) temporal_pass_kernel(const __grid_constant__ CUtensorMap tm_src,
+__global__ void __launch_bounds__(SDFG_TP_MAXT, SDFG_TP_MINB) temporal_pass_kernel(const __grid_constant__ CUtensorMap tm_src,
                                                             ST *__restrict__ dst, GridGeo g, int res_flags,
                                                             double2 *__restrict__ partials, int *err,
                                                             unsigned long long timeout_ns) {
@@ -103,7 +110,8 @@ size_t temporal_smem_bytes(int dtype, int warps) {
 
 template <class ST, int K>
 static const void *tp_fn() {
-    return reinterpret_cast<const void *>(&temporal_pass_kernel<ST, Store<ST>::bytes == 8 ? 2 : 4, K>);
+    return reinterpret_cast<const void *>(
+        &temporal_pass_kernel<ST, Store<ST>::bytes == 8 ? 2 : (Store<ST>::bytes == 4 ? SDFG_F32_V : 4), K>);
 }
 
 static const void *temporal_fn(int dtype, int k) {
@@ -154,7 +162,8 @@ int launch_temporal_pass(const CUtensorMap *tm_src, void *dst, const GridGeo &g,
                          cudaStream_t s) {
     const void *fn = temporal_fn(dtype, k);
     if (!fn) return set_error(SDFG_ERR_INVAL, "no temporal kernel for dtype %d, k=%d", dtype, k);
-    if (warps < 1 || warps > MAX_WARPS) return set_error(SDFG_ERR_INVAL, "warps per CTA must be 1..%d", MAX_WARPS);
+    if (warps < 1 || warps > MAX_WARPS || warps * 32 > SDFG_TP_MAXT)
+        return set_error(SDFG_ERR_INVAL, "warps per CTA must be 1..%d", SDFG_TP_MAXT / 32);
     const size_t smem = temporal_smem_bytes(dtype, warps);
     int rc = prepare_fn(fn, smem);
     if (rc != SDFG_OK) return rc;

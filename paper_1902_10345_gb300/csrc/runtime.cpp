@@ -180,8 +180,13 @@ std::vector<Rec> g_recs;
 const char *kFamilies[FAM_COUNT] = {"naive", "temporal", "persistent", "reduce", "copy"};
 }  // namespace
 
+static thread_local bool g_stats_suspended = false;
+
+void stats_suspend(bool on) { g_stats_suspended = on; }
+
 TimedLaunch stats_begin(int family, cudaStream_t s) {
     TimedLaunch t;
+    if (g_stats_suspended) return t;
     {
         std::lock_guard<std::mutex> lk(g_stats_mu);
         if (!g_stats_on) return t;

@@ -74,6 +74,8 @@ struct TimedLaunch {
 };
 enum Family { FAM_NAIVE = 0, FAM_TEMPORAL, FAM_PERSISTENT, FAM_REDUCE, FAM_COPY, FAM_COUNT };
 TimedLaunch stats_begin(int family, cudaStream_t s);
+// No launch is timed on this thread while suspended (stream capture).
+void stats_suspend(bool on);
 void stats_end(TimedLaunch &t, cudaStream_t s);
 
 // ---- kernel launchers (kernels.cu) -------------------------------------------

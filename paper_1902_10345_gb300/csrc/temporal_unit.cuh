@@ -95,11 +95,10 @@ __device__ __forceinline__ void storage_round(typename Store<ST>::CT (&o)[V]) {
     }
 }
 
-// A chunk wait ran out at step i: give the copies already in flight a short
+// A chunk wait ran out at chunk c0: give the copies already in flight a short
 // bounded chance to land (so none writes shared memory after the warp has
 // left), then report failure.
-__device__ __noinline__ inline bool drain_after_timeout(uint64_t *bars, uint32_t base, int n_chunks, int i) {
-    const int c0 = i / CHUNK_ROWS;
+__device__ __noinline__ inline bool drain_after_timeout(uint64_t *bars, uint32_t base, int n_chunks, int c0) {
     for (int c = c0; c < n_chunks && c < c0 + STAGES; ++c) {
         const uint32_t g = base + static_cast<uint32_t>(c);
         mbar_wait_bounded(&bars[g % STAGES], (g / STAGES) & 1u, 1000000ull);
@@ -109,7 +108,13 @@ __device__ __noinline__ inline bool drain_after_timeout(uint64_t *bars, uint32_t
 }
 
 // ---------------------------------------------------------- the unit pipe --
-template <class ST, int V, int K, bool COLCHK>
+// Rows are consumed in chunks of CHUNK_ROWS (6 = two turns of the 3-slot
+// register rotation), so one chunk is one straight-line block: all of its
+// levels and rows can be interleaved by the compiler (level l of row i+1 only
+// depends on level l-1 of rows i-1..i+1).  Chunks away from the grid's top and
+// bottom rows and inside the unit's output rows take the FAST body, with no
+// boundary or range test at all.
+template <class ST, int V, int K, bool COLCHK, bool RES>
 struct UnitPipe {
     using CT = typename Store<ST>::CT;
     static constexpr int W = 32 * V;
@@ -150,45 +155,40 @@ struct UnitPipe {
         g = g + sum;
     }
 
-    __device__ __forceinline__ void store_row(int row, const CT (&o)[V]) {
-        ST *p = dst + static_cast<size_t>(row) * ld + (X + lane * V);
-        if (full_vec) {
-            VecIO<ST, V>::store(p, o);
-        } else {
+    // Store one output row at `p` (= row start + X + lane*V).  Away from
+    // the boundary columns every owned lane holds V in-grid columns, so the
+    // store is one predicated vector instruction.
+    __device__ __forceinline__ void store_row(ST *p, const CT (&o)[V]) {
+        if (!COLCHK) {
+            store_pred(p, o, own_lane ? 1 : 0);
+        } else if (own_lane) {
+            if (full_vec) {
+                VecIO<ST, V>::store(p, o);
+            } else {
 #pragma unroll
-            for (int e = 0; e < V; ++e)
-                if (X + lane * V + e < C) p[e] = from_ct<ST>(o[e]);
+                for (int e = 0; e < V; ++e)
+                    if (X + lane * V + e < C) p[e] = from_ct<ST>(o[e]);
+            }
         }
     }
 
-    template <int PH>
-    __device__ __forceinline__ bool step(int i) {
+    // One input row r (level 0 from shared memory at `src`), all K levels.
+    template <int PH, bool SLOW>
+    __device__ __forceinline__ void step(int r, const ST *src, ST *out) {
         constexpr int SN = (PH + 1) % 3;  // slot of the north row
         constexpr int SC = (PH + 2) % 3;  // slot of the centre row
         constexpr int SS = PH;            // slot of the south (newest) row
-        const int c = i / CHUNK_ROWS;
-        const int rr = i - c * CHUNK_ROWS;
-        const uint32_t g = base + static_cast<uint32_t>(c);
-        const uint32_t slot = g % STAGES;
-        if (rr == 0) {
-            // every lane waits (acquiring the TMA-written rows); the outcome is
-            // made warp-uniform so no lane is left behind in a shuffle
-            const bool ok = mbar_wait_bounded(&bars[slot], (g / STAGES) & 1u, timeout_ns);
-            if (!__all_sync(FULL_MASK, ok)) return false;
-        }
         {
             CT tmp[V];
-            VecIO<ST, V>::load(tmp, ring + (slot * CHUNK_ROWS + rr) * W + lane * V);
+            VecIO<ST, V>::load(tmp, src);
 #pragma unroll
             for (int e = 0; e < V; ++e) b[0][SS][e] = tmp[e];
         }
-        const int r = rb + i;
-        const bool rowchk = (r <= K) || (r >= R);
 #pragma unroll
         for (int l = 0; l < K; ++l) {
             CT o[V];
             level_row<V, COLCHK>(o, b[l][SN], b[l][SC], b[l][SS], colmask);
-            if (rowchk) {
+            if (SLOW) {
                 const int rc = r - l - 1;  // row index of this level's centre
                 if (rc <= 0 || rc >= R - 1) {
 #pragma unroll
@@ -196,33 +196,48 @@ struct UnitPipe {
                 }
             }
             storage_round<ST, V>(o);
-            if (l == 0 && (res_flags & 1)) {
+            if (RES && l == 0 && (res_flags & 1)) {
                 const int row = r - 1;
                 if (row >= y0 && row < y1) accumulate(g_ref, o, b[0][SC]);
             }
             if (l == K - 1) {
                 const int row = r - K;
-                if (row >= y0 && row < y1) {
-                    if (res_flags & 2) accumulate(g_chk, o, b[l][SC]);
-                    if (own_lane) store_row(row, o);
+                if (!SLOW || (row >= y0 && row < y1)) {
+                    if (RES && (res_flags & 2)) accumulate(g_chk, o, b[l][SC]);
+                    store_row(out, o);
                 }
             } else {
 #pragma unroll
                 for (int e = 0; e < V; ++e) b[l + 1][SS][e] = o[e];
             }
         }
-        if (rr == CHUNK_ROWS - 1 || i == n_steps - 1) {
-            // every lane has consumed chunk c: recycle its slot
-            __syncwarp();
-            if (lane == 0 && c + STAGES < n_chunks) issue(c + STAGES);
-            if (res_flags) {
-                acc_ref += static_cast<double>(g_ref);
-                acc_chk += static_cast<double>(g_chk);
-                g_ref = CT(0);
-                g_chk = CT(0);
-            }
+    }
+
+    // `out` points at output row r0-K (it is only dereferenced for rows the
+    // unit owns).
+    template <bool SLOW>
+    __device__ __forceinline__ void chunk_body(int r0, const ST *src, ST *out) {
+        static_assert(CHUNK_ROWS == 6, "chunk body is written for 6 rows");
+        const size_t ldr = static_cast<size_t>(ld);
+#ifdef SDFG_HALF_BODY
+        // two turns of one 3-row body (smaller hot loop)
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            step<0, SLOW>(r0 + 0, src + 0 * W, out);
+            step<1, SLOW>(r0 + 1, src + 1 * W, out + ldr);
+            step<2, SLOW>(r0 + 2, src + 2 * W, out + 2 * ldr);
+            r0 += 3;
+            src += 3 * W;
+            out += 3 * ldr;
         }
-        return true;
+#else
+        step<0, SLOW>(r0 + 0, src + 0 * W, out);
+        step<1, SLOW>(r0 + 1, src + 1 * W, out + ldr);
+        step<2, SLOW>(r0 + 2, src + 2 * W, out + 2 * ldr);
+        step<0, SLOW>(r0 + 3, src + 3 * W, out + 3 * ldr);
+        step<1, SLOW>(r0 + 4, src + 4 * W, out + 4 * ldr);
+        step<2, SLOW>(r0 + 5, src + 5 * W, out + 5 * ldr);
+#endif
     }
 
     __device__ __forceinline__ bool run() {
@@ -232,20 +247,43 @@ struct UnitPipe {
             for (int s = 0; s < 3; ++s)
 #pragma unroll
                 for (int e = 0; e < V; ++e) b[l][s][e] = CT(0);
-        g_ref = g_chk = CT(0);
-        acc_ref = acc_chk = 0.0;
+        if (RES) {
+            g_ref = g_chk = CT(0);
+            acc_ref = acc_chk = 0.0;
+        }
         if (lane == 0) {
             const int first = n_chunks < STAGES ? n_chunks : STAGES;
             for (int c = 0; c < first; ++c) issue(c);
         }
-        int i = 0;
-        for (; i + 2 < n_steps; i += 3) {
-            if (!step<0>(i)) return drain_after_timeout(bars, base, n_chunks, i);
-            if (!step<1>(i + 1)) return drain_after_timeout(bars, base, n_chunks, i + 1);
-            if (!step<2>(i + 2)) return drain_after_timeout(bars, base, n_chunks, i + 2);
+        for (int c = 0; c < n_chunks; ++c) {
+            const uint32_t g = base + static_cast<uint32_t>(c);
+            const uint32_t slot = g % STAGES;
+            // every lane waits (acquiring the TMA-written rows); the outcome is
+            // made warp-uniform so no lane is left behind in a shuffle
+            const bool ok = mbar_wait_bounded(&bars[slot], (g / STAGES) & 1u, timeout_ns);
+            if (!__all_sync(FULL_MASK, ok)) return drain_after_timeout(bars, base, n_chunks, c);
+            const int r0 = rb + c * CHUNK_ROWS;
+            const ST *src = ring + slot * (CHUNK_ROWS * W) + lane * V;
+            // Rows past the unit's last step are in the box (zero-filled past
+            // the grid) and only produce rows that are never stored.
+            const bool fast = (r0 >= K + 1) && (r0 + CHUNK_ROWS <= R) && (r0 - K >= y0) &&
+                              (r0 + CHUNK_ROWS - K <= y1);
+            // pointer arithmetic only: rows before 0 are never dereferenced
+            ST *out = dst + (static_cast<ptrdiff_t>(r0) - K) * ld + (X + lane * V);
+            if (fast)
+                chunk_body<false>(r0, src, out);
+            else
+                chunk_body<true>(r0, src, out);
+            // every lane has consumed chunk c: recycle its slot
+            __syncwarp();
+            if (lane == 0 && c + STAGES < n_chunks) issue(c + STAGES);
+            if (RES) {
+                acc_ref += static_cast<double>(g_ref);
+                acc_chk += static_cast<double>(g_chk);
+                g_ref = CT(0);
+                g_chk = CT(0);
+            }
         }
-        if (i < n_steps && !step<0>(i)) return drain_after_timeout(bars, base, n_chunks, i);
-        if (i + 1 < n_steps && !step<1>(i + 1)) return drain_after_timeout(bars, base, n_chunks, i + 1);
         return true;
     }
 };
@@ -283,18 +321,22 @@ __device__ __forceinline__ bool run_unit(const void *tmap, ST *dst, const GridGe
 
     bool ok;
     double ar = 0.0, ac = 0.0;
-#define SDFG_RUN_PIPE(CHK)                                                                              \
+#define SDFG_RUN_PIPE(CHK, RS)                                                                          \
     {                                                                                                   \
-        UnitPipe<ST, V, K, CHK> p;                                                                      \
+        UnitPipe<ST, V, K, CHK, RS> p;                                                                  \
         p.tmap = tmap; p.dst = dst; p.ld = g.ld; p.R = g.R; p.C = g.C;                                  \
         p.X = X; p.y0 = y0; p.y1 = y1; p.rb = rb; p.n_steps = n_steps; p.n_chunks = n_chunks;           \
         p.base = chunk_ctr; p.ring = ring; p.bars = bars; p.lane = lane;                                \
         p.colmask = colmask; p.resmask = resmask; p.own_lane = own_lane; p.full_vec = full_vec;         \
         p.res_flags = res_flags; p.timeout_ns = timeout_ns;                                             \
         ok = p.run();                                                                                   \
-        ar = p.acc_ref; ac = p.acc_chk;                                                                 \
+        if (RS) { ar = p.acc_ref; ac = p.acc_chk; }                                                     \
     }
-    if (colchk) SDFG_RUN_PIPE(true) else SDFG_RUN_PIPE(false)
+    if (res_flags) {
+        if (colchk) SDFG_RUN_PIPE(true, true) else SDFG_RUN_PIPE(false, true)
+    } else {
+        if (colchk) SDFG_RUN_PIPE(true, false) else SDFG_RUN_PIPE(false, false)
+    }
 #undef SDFG_RUN_PIPE
     chunk_ctr += static_cast<uint32_t>(n_chunks);
 
