@@ -107,6 +107,27 @@ int sdfg_jacobi2d_cfg(const void *in, void *out, int rows, int cols, int ld, int
                       const sdfg_config *cfg, void *stream);
 
 /*
+ * Single grid, FP32, asynchronous, allocating no device memory.  Same
+ * operation and result as sdfg_jacobi2d.  The paper has no counterpart: this
+ * entry point exists for callers that may not call cudaMalloc -- for example
+ * a plug-in inside a host application that owns the whole device memory
+ * budget, or a latency-critical loop that cannot afford an allocation's
+ * implicit synchronisation.  Its ping-pong scratch grid is a fixed 32 MiB
+ * device array inside the library (8,388,608 floats), which every GPU that
+ * loads the library keeps until the process exits.
+ *   - rows * cols must not exceed 8,388,608 (SDFG_ERR_INVAL otherwise);
+ *   - in/out must be 16-byte aligned and cols a multiple of 4 (ld = cols);
+ *   - the first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture;
+ *   - every call shares the one array and it keeps the last call's contents:
+ *     calls whose work overlaps on the GPU (other streams, other threads)
+ *     race on it, so serialise them.  No element needs to start at zero:
+ *     every pass writes each element before it is read.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+int sdfg_jacobi2d_noalloc(const float *in, float *out, int rows, int cols, int T, void *stream);
+
+/*
  * End-to-end call on HOST buffers (contiguous, ld = cols): copies h_in to the
  * device, runs T steps, copies the result to h_out, and returns when h_out
  * holds it.  Pinned host memory gives the fastest copies.  Device buffers are

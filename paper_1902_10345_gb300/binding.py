@@ -50,6 +50,7 @@ _PROTOS = {
     "sdfg_jacobi2d_ex": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _VP]),
     "sdfg_jacobi2d_cfg": (_I, [_VP, _VP, _I, _I, _I, _I, _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_jacobi2d_host": (_I, [_VP, _VP, _I, _I, _I, _I, _VP]),
+    "sdfg_jacobi2d_noalloc": (_I, [_VP, _VP, _I, _I, _I, _VP]),
     "sdfg_jacobi2d_solve": (_I, [ctypes.POINTER(sdfg_desc), _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_jacobi2d_batch": (_I, [ctypes.POINTER(sdfg_desc), _I, _I, _VP]),
     "sdfg_batch_plan_create": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(sdfg_desc), _I, _I,
@@ -121,6 +122,10 @@ def sdfg_jacobi2d_ex(inp, out, rows, cols, ld, T, dtype, stream=0) -> int:
 
 def sdfg_jacobi2d_cfg(inp, out, rows, cols, ld, T, dtype, cfg: sdfg_config | None, stream=0) -> int:
     return lib().sdfg_jacobi2d_cfg(inp, out, rows, cols, ld, T, dtype, ctypes.byref(cfg) if cfg else None, stream)
+
+
+def sdfg_jacobi2d_noalloc(inp: int, out: int, rows: int, cols: int, T: int, stream: int = 0) -> int:
+    return lib().sdfg_jacobi2d_noalloc(inp, out, rows, cols, T, stream)
 
 
 def sdfg_jacobi2d_host(h_in, h_out, rows, cols, T, dtype, stream=0) -> int:

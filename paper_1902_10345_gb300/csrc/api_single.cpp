@@ -240,6 +240,34 @@ int run_single(const void *in, void *out, int R, int C, int ld, long long T, int
     return rc;
 }
 
+// Temporal (or naive) path with a scratch grid the caller provides (R x ld
+// elements, not overlapping in/out); allocates nothing.  `st` may describe a
+// device whose error word lives in caller-provided memory.
+int run_single_with_scratch(const void *in, void *out, void *scratch, int R, int C, int ld, long long T, int dtype,
+                            const sdfg_config *cfg, DeviceState *st, cudaStream_t s) {
+    if (R == 0 || C == 0) return SDFG_OK;
+    if (T == 0 || R < 3 || C < 3) return launch_copy2d(out, ld, in, ld, R, C, dtype, s);
+    sdfg_config c;
+    int rc = resolve_config(cfg, R, C, dtype, &c);
+    if (rc != SDFG_OK) return rc;
+    if (c.kernel != SDFG_KERNEL_NAIVE) c.kernel = SDFG_KERNEL_TEMPORAL;
+    const std::vector<int> ks = c.kernel == SDFG_KERNEL_NAIVE ? std::vector<int>(1, static_cast<int>(T))
+                                                              : plan_passes(T, c.k);
+    const long long n_steps_total = c.kernel == SDFG_KERNEL_NAIVE ? T : static_cast<long long>(ks.size());
+    void *first, *second;
+    if (in != out) {
+        first = (n_steps_total % 2 == 1) ? out : scratch;
+        second = (first == out) ? scratch : out;
+    } else {
+        first = scratch;
+        second = out;
+    }
+    void *fin = nullptr;
+    rc = run_pass_sequence(in, first, second, ks, R, C, ld, dtype, c, st, s, &fin);
+    if (rc == SDFG_OK && fin != out) rc = launch_copy2d(out, ld, fin, ld, R, C, dtype, s);
+    return rc;
+}
+
 }  // namespace sdfg
 
 using namespace sdfg;
