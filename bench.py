@@ -37,7 +37,7 @@ UNIT = "GUpdates/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--rows", type=int, default=8192)
@@ -46,8 +46,14 @@ def parse():
     p.add_argument("--k", type=int, default=0, help="fused depth (0 = library default / autotuned)")
     p.add_argument("--warps", type=int, default=0)
     p.add_argument("--seg-rows", type=int, default=0)
+    p.add_argument("--kernel", choices=["persistent", "temporal"], default="persistent")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--workload", choices=["single", "batch", "precision", "serve"], default="single",
+                   help="single: 8192^2 FP32 T=1000 (the default line); batch: 512 uneven grids in one "
+                        "persistent launch; precision: 4 x 16384^2 T=500 FP32 and BF16; serve: Laplace requests")
+    p.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
+    p.add_argument("--rho", type=float, default=0.9, help="serve: arrival rate as a fraction of served capacity")
     return p.parse_args()
 
 
@@ -94,7 +100,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(CLOCK_FIELDS),
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -250,7 +256,9 @@ def run_ours(a):
     g = inputs.uniform_grid(R, C, seed=0)
     x = torch.from_numpy(g).float().cuda()
     y = torch.empty_like(x)
-    cfg = binding.config(kernel=binding.SDFG_KERNEL_AUTO, k=a.k, seg_rows=a.seg_rows, warps=a.warps)
+    # the launch configuration timed here (and used by the full-size parity test)
+    cfg = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT if a.kernel == "persistent" else
+                         binding.SDFG_KERNEL_TEMPORAL, k=a.k or 8, seg_rows=a.seg_rows or 128, warps=a.warps or 4)
     stream = torch.cuda.current_stream()
     updates = (R - 2) * (C - 2) * T
 
@@ -301,25 +309,33 @@ def run_ours(a):
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (temporal pass): algorithmic bytes per
-    # launch = interior points x 2 x 4 B (one read + one write per pass)
-    n_tp, ms_tp = launches["temporal"]
+    # roofline of the dominant kernel: algorithmic bytes = interior points x
+    # 2 x 4 B per pass (one read + one write per pass of k fused steps)
+    fam = max(("temporal", "persistent"), key=lambda f: launches[f][1])
+    n_tp, ms_tp = launches[fam]
     hbm, hbm_src = measured_peaks()
-    bytes_per_launch = (R - 2) * (C - 2) * 2 * 4
+    k_used = cfg.k
+    passes_per_step = -(-T // k_used)
+    bytes_per_launch = (R - 2) * (C - 2) * 2 * 4 * (passes_per_step if fam == "persistent" else 1)
     achieved = bytes_per_launch / (ms_tp / n_tp / 1e3) / 1e9 if n_tp else None
+    # FP32-pipe ceiling: 5 FP32 lane-ops per update on 152 SMs x 128 lanes at the max SM clock
+    alu_peak = 152 * 128 * 2.07e9 / 1e12
+    alu_achieved = 5 * value / 1e3
     from paper_1902_10345_gb300 import build as _b
-    digest = _b._digest()[:16]
+    digest = _b.kernel_digest()
     traffic = committed_traffic(digest, workload_name(a))
-    k_used = a.k or 8
-    n_pass = n_tp // a.steps if n_tp else 0
     gpu_launches = sum(v[0] for v in launches.values())
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
             "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src,
-            "kernel": "temporal_pass_kernel", "k": k_used, "passes_per_step": n_pass,
+            "kernel": f"{fam}_kernel", "k": k_used, "passes_per_step": passes_per_step,
+            "launches_per_step": n_tp / a.steps if n_tp else 0,
             "avg_launch_ms": (ms_tp / n_tp) if n_tp else None,
             "roofline_gupdates": hbm * k_used / (2 * 4),
-            "kernel_share_of_step": (ms_tp / ms) if ms else None}
+            "kernel_share_of_step": (ms_tp / ms) if ms else None,
+            "secondary": {"bound": "alu", "unit": "TFLOP/s", "achieved": alu_achieved, "peak": alu_peak,
+                          "frac": alu_achieved / alu_peak,
+                          "note": "5 FP32 ops per useful update vs 152 SMs x 128 FP32 lanes x 2.07 GHz"}}
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         cpu = cpu_oracle_sample(a, a.cpu_seconds)
@@ -328,6 +344,7 @@ def run_ours(a):
         "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(a), "rows": R, "cols": C, "T": T, "k": k_used,
+                   "kernel": a.kernel, "seg_rows": cfg.seg_rows, "warps_per_cta": cfg.warps,
                    "l2": "inputs larger than L2 (two 256 MiB grids), no flush", "parallelism": f"replicas{world}"},
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -339,10 +356,259 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------- batch -------
+def _padded(R, C, dtype, device="cuda"):
+    import torch
+    ld = (C + 3) // 4 * 4
+    return torch.zeros((R, ld), dtype=dtype, device=device)[:, :C]
+
+
+def run_batch(a):
+    """512 uneven grids (rows, cols log-uniform in [64, 2048], T in [50, 500])
+    in ONE persistent launch, replayed through a captured CUDA graph."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_1902_10345_gb300 import binding, build, inputs
+
+    build.build()
+    L = binding.lib()
+    specs = inputs.batch_specs(512, seed=0)
+    xs, ys, descs = [], [], []
+    for sp in specs:
+        x = _padded(sp.rows, sp.cols, torch.float32)
+        x.copy_(torch.from_numpy(inputs.batch_grid(sp)).float())
+        y = _padded(sp.rows, sp.cols, torch.float32)
+        xs.append(x)
+        ys.append(y)
+        descs.append(binding.desc_for(x, y, sp.T))
+    updates = sum((sp.rows - 2) * (sp.cols - 2) * sp.T for sp in specs)
+    if a.k or a.seg_rows:
+        cfg = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=a.k or 8, seg_rows=a.seg_rows or 96,
+                             warps=a.warps or 4)
+        tuned = False
+    else:
+        # the project's autotuner picks k and the segment height on this batch
+        cfg = binding.sdfg_autotune_batch(descs, 64)
+        tuned = True
+    arr = (binding.sdfg_desc * len(descs))(*descs)
+    plan = ctypes.c_void_p()
+    stream = torch.cuda.current_stream()
+    binding.check(L.sdfg_batch_plan_create(ctypes.byref(plan), arr, len(descs), 64, ctypes.byref(cfg), 0))
+    for _ in range(max(3, a.warmup)):
+        binding.check(L.sdfg_batch_plan_run(plan, stream.cuda_stream))
+    binding.check(L.sdfg_batch_plan_results(plan, arr, len(descs)))
+    binding.sdfg_stats_reset()
+    binding.sdfg_stats_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(a.steps):
+            binding.check(L.sdfg_batch_plan_run(plan, stream.cuda_stream))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    binding.sdfg_stats_enable(False)
+    binding.check(L.sdfg_batch_plan_results(plan, arr, len(descs)))
+    ms = e0.elapsed_time(e1)
+    n_pk, ms_pk = binding.sdfg_stats_get("persistent")   # graph replays are not split per kernel
+    binding.check(L.sdfg_batch_plan_destroy(plan))
+    value = updates * a.steps / (ms / 1e3) / 1e9
+    k = cfg.k
+    passes = sum(-(-sp.T // k) for sp in specs)
+    bytes_per_step = sum((sp.rows - 2) * (sp.cols - 2) * 2 * 4 * -(-sp.T // k) for sp in specs)
+    hbm, src = measured_peaks()
+    achieved = bytes_per_step / (ms / a.steps / 1e3) / 1e9
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": max(3, a.warmup),
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "jacobi2d_batch512_uneven_f32", "grids": 512, "updates_per_step": updates,
+                   "k": k, "seg_rows": cfg.seg_rows, "autotuned": tuned, "passes_per_step": passes,
+                   "layout": "each grid pitched to a multiple of 4 columns (16-byte rows)",
+                   "l2": "1.3 GB resident, larger than L2, no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "kernel": "persistent_kernel (graph replay; whole step timed)",
+                     "roofline_gupdates": hbm * k / 8},
+        "clocks": clk.summary(), "gpu_launches": 2 * a.steps,
+    }))
+
+
+# --------------------------------------------------------------- precision -------
+def run_precision(a):
+    """4 grids of 16384^2, T=500, sinusoid field; FP32 and BF16 storage.
+    Throughput of each, and the error of each result against the FP64 oracle
+    on light-cone windows (exact for the windows)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1902_10345_gb300 import binding, build, inputs
+
+    build.build()
+    binding.lib()
+    n, T, W = 16384, 500, 40
+    rng = np.random.default_rng(12345)
+    out = {}
+    stream = torch.cuda.current_stream()
+    for dt_name, tdt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        ms_total, errs, sq, cnt, q_err = 0.0, [], 0.0, 0, 0.0
+        for seed in range(4):
+            f64 = inputs.sinusoid_field_device(n, seed=seed)
+            x = f64.to(tdt)
+            q_err = max(q_err, float((x.double() - f64).abs().max()))
+            del f64
+            y = torch.empty_like(x)
+            binding.jacobi2d(x, y, T)                       # warm-up / plan
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            binding.jacobi2d(x, y, T)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_total += e0.elapsed_time(e1)
+            for _ in range(3):
+                r0 = int(rng.integers(0, n - W))
+                c0 = int(rng.integers(0, n - W))
+                m = T + 1
+                cr0, cr1, cc0, cc1 = max(0, r0 - m), min(n, r0 + W + m), max(0, c0 - m), min(n, c0 + W + m)
+                crop = x[cr0:cr1, cc0:cc1].double().cpu().numpy()
+                want = oracle.jacobi2d(crop, T, threads=0)[r0 - cr0:r0 - cr0 + W, c0 - cc0:c0 - cc0 + W]
+                got = y[r0:r0 + W, c0:c0 + W].double().cpu().numpy()
+                d = got - want
+                errs.append(float(np.abs(d).max()))
+                sq += float((d * d).sum())
+                cnt += d.size
+            del x, y
+            torch.cuda.empty_cache()
+        updates = 4 * (n - 2) * (n - 2) * T
+        out[dt_name] = {"gupdates_per_s": updates / (ms_total / 1e3) / 1e9, "ms": ms_total,
+                        "max_abs_err": max(errs), "rms_err": (sq / cnt) ** 0.5,
+                        "input_quantisation_max_abs": q_err,
+                        "windows": f"{len(errs)} windows of {W}x{W} (FP64 oracle on light-cone crops)"}
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "precision_4x16384sq_T500_sinusoid",
+                      "results": out, "tolerance": {"f32": 1e-4, "bf16": 2e-2}}))
+
+
+# ------------------------------------------------------------------- serve -------
+def _pct(v, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def run_serve(a):
+    """Served Laplace solves: requests with sides log-uniform in [32, 4096],
+    boundary x^2 - y^2 + noise, zero interior, FP32, relative residual 1e-6 or
+    20000 steps, 40 GB budget.  Capacity first (all requests at t=0), then a
+    Poisson arrival trace at rho x capacity replayed against (1) the
+    continuous-batching server and (2) plain launches: one blocking solve per
+    request in arrival order."""
+    import ctypes
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_1902_10345_gb300 import binding, build, inputs
+
+    build.build()
+    L = binding.lib()
+    n = a.requests
+    reqs = inputs.served_requests(n, seed=0)
+    xs = [inputs.laplace_request_grid_device(r, dtype=torch.float32) for r in reqs]
+    ys = [torch.zeros_like(x) for x in xs]
+    tol, cap, stride, quantum = 1e-6, 20000, 64, 256
+    budget = 40 << 30
+
+    def serve(arrivals):
+        sv = ctypes.c_void_p()
+        binding.check(L.sdfg_server_create(ctypes.byref(sv), budget, 1024, quantum, stride, 0))
+        ids = [None] * n
+        sub_t = [0.0] * n
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i in np.argsort(arrivals, kind="stable"):
+                dt = t0 + arrivals[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                d = binding.desc_for(xs[i], ys[i], cap, tol)
+                rid = ctypes.c_uint64()
+                binding.check(L.sdfg_server_submit(sv, ctypes.byref(d), ctypes.byref(rid)))
+                sub_t[i] = time.perf_counter()
+                ids[i] = rid.value
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        done_t = [None] * n
+        steps = [0] * n
+        res = binding.sdfg_desc()
+        left = n
+        while left:
+            for i in range(n):
+                if done_t[i] is None and ids[i] is not None:
+                    rc = L.sdfg_server_poll(sv, ids[i], ctypes.byref(res))
+                    if rc != binding.SDFG_PENDING:
+                        binding.check(rc)
+                        done_t[i] = time.perf_counter()
+                        steps[i] = res.steps_done
+                        left -= 1
+            time.sleep(0.0005)
+        th.join()
+        binding.check(L.sdfg_server_destroy(sv))
+        lat = [done_t[i] - (t0 + arrivals[i]) for i in range(n)]
+        span = max(done_t) - t0
+        return lat, steps, span
+
+    def plain(arrivals):
+        t0 = time.perf_counter()
+        lat, steps, done = [0.0] * n, [0] * n, 0.0
+        for i in np.argsort(arrivals, kind="stable"):
+            dt = t0 + arrivals[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            d = binding.desc_for(xs[i], ys[i], cap, tol)
+            binding.check(binding.sdfg_jacobi2d_solve(d, stride))
+            done = time.perf_counter()
+            lat[i] = done - (t0 + arrivals[i])
+            steps[i] = d.steps_done
+        return lat, steps, done - t0
+
+    def gups(steps, span):
+        return sum((r.rows - 2) * (r.cols - 2) * s for r, s in zip(reqs, steps)) / span / 1e9
+
+    # capacity: everything queued at t = 0
+    lat0, steps0, span0 = serve(np.zeros(n))
+    capacity = n / span0
+    rate = a.rho * capacity
+    arrivals = inputs.poisson_arrivals(n, rate, seed=1)
+    lat_s, steps_s, span_s = serve(arrivals)
+    lat_p, steps_p, span_p = plain(arrivals)
+    print(json.dumps({
+        "metric": METRIC, "unit": UNIT, "workload": f"served_laplace_{n}req_32to4096_tol1e-6_cap20000_f32",
+        "capacity_req_per_s": capacity, "capacity_gupdates": gups(steps0, span0), "rho": a.rho,
+        "arrival_rate_hz": rate,
+        "server": {"p50_s": _pct(lat_s, 50), "p99_s": _pct(lat_s, 99), "gupdates": gups(steps_s, span_s),
+                   "makespan_s": span_s},
+        "plain_launches": {"p50_s": _pct(lat_p, 50), "p99_s": _pct(lat_p, 99), "gupdates": gups(steps_p, span_p),
+                           "makespan_s": span_p},
+        "steps_equal_server_vs_plain": sum(int(a_ == b_) for a_, b_ in zip(steps_s, steps_p)),
+        "budget_bytes": budget, "quantum_steps": quantum, "check_stride": stride,
+    }))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch":
+        run_batch(a)
+    elif a.workload == "precision":
+        run_precision(a)
+    elif a.workload == "serve":
+        run_serve(a)
     else:
         run_ours(a)
 

@@ -18,12 +18,14 @@
  * steps, boundary included.  Every update is evaluated in the order shown,
  * with IEEE round-to-nearest and no fused multiply-add, so FP32 and FP64
  * results do not depend on tiling, on the number of fused steps, or on what
- * else runs in the same batch.  FP64 results equal a plain FP64 loop bit for
- * bit.
+ * else runs in the same batch (BF16 results depend only on the number of fused
+ * steps).  FP64 results equal a plain FP64 loop bit for bit.
  *
- * Storage types: FP32 (arithmetic FP32), BF16 (arithmetic FP32; every
- * timestep's result is rounded to BF16 with round-to-nearest-even, as if the
- * array were written back after each step), FP64 (arithmetic FP64).
+ * Storage types: FP32 (arithmetic FP32), BF16 (the grid is stored in BF16;
+ * arithmetic is FP32, and the steps fused into one pass stay in FP32
+ * registers, so values are rounded to BF16 (nearest-even) each time a pass
+ * writes the grid -- every k steps, or every step for the naive kernel; the
+ * result therefore depends on k), FP64 (arithmetic FP64).
  *
  * Layout: row-major, `ld` elements between the starts of consecutive rows
  * (ld >= cols).  All grid pointers are DEVICE pointers unless a function says
@@ -205,6 +207,13 @@ int sdfg_server_destroy(sdfg_server *server);
 /* Autotuner: times candidate configurations for this shape and dtype on the
  * calling stream, caches the best by shape class, and returns it. */
 int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *best, void *stream);
+
+/* Batch autotuner: times candidate (k, segment height) plans of the
+ * persistent kernel on the caller's batch (the grids are overwritten by the
+ * trial runs), caches the best for batches of this class (dtype, grid count,
+ * mean area), and returns it.  Plans created afterwards with cfg == NULL for
+ * a batch of the same class use it. */
+int sdfg_autotune_batch(const sdfg_desc *desc, int n, int check_stride, sdfg_config *best, void *stream);
 
 /* Per-kernel CUDA-event timing inside the library (off by default).  While
  * enabled, every launch is bracketed by events on its own stream. */

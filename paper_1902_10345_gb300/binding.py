@@ -64,6 +64,7 @@ _PROTOS = {
     "sdfg_server_drain": (_I, [_VP, _I]),
     "sdfg_server_destroy": (_I, [_VP]),
     "sdfg_autotune": (_I, [_I, _I, _I, _I, ctypes.POINTER(sdfg_config), _VP]),
+    "sdfg_autotune_batch": (_I, [ctypes.POINTER(sdfg_desc), _I, _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_stats_enable": (_I, [_I]),
     "sdfg_stats_reset": (_I, []),
     "sdfg_stats_get": (_I, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
@@ -152,6 +153,13 @@ def sdfg_jacobi2d_batch(descs, check_stride: int, stream=0) -> int:
 def sdfg_autotune(rows, cols, T, dtype, stream=0) -> sdfg_config:
     c = sdfg_config()
     check(lib().sdfg_autotune(rows, cols, T, dtype, ctypes.byref(c), stream))
+    return c
+
+
+def sdfg_autotune_batch(descs, check_stride: int, stream=0) -> sdfg_config:
+    arr = (sdfg_desc * len(descs))(*descs)
+    c = sdfg_config()
+    check(lib().sdfg_autotune_batch(arr, len(descs), check_stride, ctypes.byref(c), stream))
     return c
 
 

@@ -24,8 +24,12 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-Xptxas", "-warn-spills"]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function"]
-# developer knob: extra nvcc flags (e.g. -DSDFG_TP_MAXT=128 -DSDFG_TP_MINB=4)
-NVCC_FLAGS += os.environ.get("SDFG_NVCC_EXTRA", "").split()
+# developer knobs: SDFG_DEFINES (e.g. "-DSDFG_CHUNK_ROWS=12 -DSDFG_STAGES=2") reaches BOTH
+# compilers, so host planning and kernels agree on shared constants;
+# SDFG_NVCC_EXTRA adds device-only flags (e.g. -DSDFG_TP_MINB=4)
+_DEFINES = os.environ.get("SDFG_DEFINES", "").split()
+NVCC_FLAGS += _DEFINES + os.environ.get("SDFG_NVCC_EXTRA", "").split()
+CXX_FLAGS += _DEFINES
 
 
 def cuda_home() -> str:
@@ -52,6 +56,21 @@ def _digest() -> str:
             h.update(fh.read())
     h.update(" ".join(NVCC_FLAGS + CXX_FLAGS).encode())
     return h.hexdigest()
+
+
+KERNEL_FILES = ["device_common.cuh", "temporal_unit.cuh", "geometry.h", "persistent.h", "persistent.cu", "kernels.cu"]
+
+
+def kernel_digest() -> str:
+    """Digest of the device sources and flags that define the kernels (used
+    to tell whether a committed profile still describes the current kernels)."""
+    h = hashlib.sha256()
+    for f in KERNEL_FILES:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    h.update(" ".join(NVCC_FLAGS).encode())
+    return h.hexdigest()[:16]
 
 
 def _compile(src: str, cuda: str, verbose: bool) -> str:

@@ -45,7 +45,11 @@ int resolve_config(const sdfg_config *cfg, int R, int C, int dtype, sdfg_config 
         return set_error(SDFG_ERR_INVAL, "bad seg_rows/warps (%d/%d)", c.seg_rows, c.warps);
     sdfg_config tuned;
     const bool have = autotune_lookup(R, C, dtype, &tuned);
-    if (c.kernel == SDFG_KERNEL_AUTO) c.kernel = have ? tuned.kernel : SDFG_KERNEL_TEMPORAL;
+    // large grids: one persistent launch for all passes (no per-pass tail);
+    // small grids: one launch per pass
+    if (c.kernel == SDFG_KERNEL_AUTO)
+        c.kernel = have ? tuned.kernel
+                        : (static_cast<long long>(R) * C >= (1LL << 20) ? SDFG_KERNEL_PERSISTENT : SDFG_KERNEL_TEMPORAL);
     if (c.k == 0) c.k = have && tuned.k ? tuned.k : default_depth(dtype);
     if (c.warps == 0) c.warps = have && tuned.warps ? tuned.warps : 4;
     if (c.seg_rows == 0 && have) c.seg_rows = tuned.seg_rows;
@@ -135,6 +139,8 @@ static int run_single_persistent(const void *in, void *out, int R, int C, int ld
         if (x->key == key) e = x;
     if (!e) {
         if (g_single.size() >= kSingleCacheSize) {
+            // the evicted plan's last launch may run on another stream
+            cudaDeviceSynchronize();
             auto it = std::min_element(g_single.begin(), g_single.end(),
                                        [](SingleEntry *a, SingleEntry *b) { return a->stamp < b->stamp; });
             (*it)->ls.release(s);
@@ -193,7 +199,7 @@ int run_single(const void *in, void *out, int R, int C, int ld, long long T, int
     const long long n_steps_total = c.kernel == SDFG_KERNEL_NAIVE ? T : static_cast<long long>(ks.size());
     const int S = dtype_bytes(dtype);
     const bool tma_ok = tma_compatible(in, ld, dtype) && tma_compatible(out, ld, dtype);
-    if (c.kernel == SDFG_KERNEL_PERSISTENT && tma_ok && !in_disposable) {
+    if (c.kernel == SDFG_KERNEL_PERSISTENT && tma_ok) {
         sdfg_config pc = c;
         if (pc.seg_rows == 0) pc.seg_rows = 128;
         if (pc.warps > 4) pc.warps = 4;

@@ -30,7 +30,11 @@ int bucket(int n) {
     return b;
 }
 
-Key key_of(int rows, int cols, int dtype) { return Key(dtype, bucket(std::max(rows, 1)), bucket(std::max(cols, 1))); }
+// Single grids key on (rows, cols); batches pass (-count, -mean area) and key
+// on negative buckets so the two never collide.
+int signed_bucket(int n) { return n < 0 ? -1 - bucket(-n) : bucket(std::max(n, 1)); }
+
+Key key_of(int rows, int cols, int dtype) { return Key(dtype, signed_bucket(rows), signed_bucket(cols)); }
 
 void load_locked() {
     if (g_loaded) return;
@@ -100,15 +104,15 @@ extern "C" int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *
     cudaEventCreate(&e1);
     // probe length: enough steps that each candidate runs a few passes
     const long long Tp = std::min<long long>(T, 64);
-    const int ks[] = {1, 2, 4, 8};
-    const int warps_c[] = {4, 8};
-    const int segs_c[] = {0, 64, 256};
+    const int ks[] = {2, 4, 8};
+    const int kernels[] = {SDFG_KERNEL_TEMPORAL, SDFG_KERNEL_PERSISTENT};
+    const int segs_c[] = {96, 128, 192};
     float best_ms = 1e30f;
-    sdfg_config winner = {SDFG_KERNEL_TEMPORAL, default_depth(dtype), 0, 8};
+    sdfg_config winner = {SDFG_KERNEL_TEMPORAL, default_depth(dtype), 0, 4};
     for (int k : ks) {
-        for (int w : warps_c) {
+        for (int kern : kernels) {
             for (int sr : segs_c) {
-                sdfg_config c = {SDFG_KERNEL_TEMPORAL, k, sr, w};
+                sdfg_config c = {kern, k, sr, 4};
                 // warm-up, then timed
                 rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);
                 if (rc != SDFG_OK) break;

@@ -331,7 +331,15 @@ static int plan_build(sdfg_batch_plan **out, const sdfg_desc *desc, int n, int c
     }
     if (any_tol && check_stride < 1) return set_error(SDFG_ERR_INVAL, "batch: check_stride must be >= 1");
     sdfg_config c = {SDFG_KERNEL_PERSISTENT, 0, 0, 0};
-    if (cfg) c = *cfg;
+    if (cfg) {
+        c = *cfg;
+    } else if (n > 0) {
+        double area = 0.0;
+        for (int g = 0; g < n; ++g) area += static_cast<double>(desc[g].rows) * desc[g].cols;
+        area /= n;
+        sdfg_config tuned;
+        if (autotune_lookup(-n, -static_cast<int>(area > 2e9 ? 2e9 : area), dtype, &tuned)) c = tuned;
+    }
     if (c.k != 0 && !depth_supported(c.k)) return set_error(SDFG_ERR_INVAL, "batch: k must be 1, 2, 4 or 8");
     if (c.warps < 0 || c.warps > MAX_WARPS || c.seg_rows < 0) return set_error(SDFG_ERR_INVAL, "batch: bad config");
     DeviceState *st = nullptr;
@@ -567,6 +575,61 @@ extern "C" int sdfg_jacobi2d_solve(sdfg_desc *desc, int check_stride, const sdfg
     if (rc == SDFG_OK) rc = plan_results(p, desc, 1);
     plan_free(p);
     return rc;
+}
+
+// ---------------------------------------------------------- batch tuner -----
+// Candidates: fused depth k in {4, 8} x segment height in {96, 128, 192}.
+// Each is built as a plan over the caller's batch, run once to warm up and
+// once timed; the fastest is cached under the batch's class (dtype, grid
+// count and mean area, both power-of-two buckets) and returned.
+extern "C" int sdfg_autotune_batch(const sdfg_desc *desc, int n, int check_stride, sdfg_config *best, void *stream) {
+    (void)stream;
+    if (!best || n < 1 || !desc) return set_error(SDFG_ERR_INVAL, "sdfg_autotune_batch: bad argument");
+    double area = 0.0;
+    for (int g = 0; g < n; ++g) area += static_cast<double>(desc[g].rows) * desc[g].cols;
+    area /= n;
+    const int dtype = desc[0].dtype;
+    const int ks[] = {4, 8};
+    const int segs[] = {96, 128, 192};
+    float best_ms = 1e30f;
+    sdfg_config winner = {SDFG_KERNEL_PERSISTENT, default_depth(dtype), 96, 4};
+    std::vector<sdfg_desc> tmp(desc, desc + n);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = SDFG_OK;
+    for (int k : ks) {
+        if (dtype == SDFG_F64 && k > 4) continue;
+        for (int seg : segs) {
+            sdfg_config c = {SDFG_KERNEL_PERSISTENT, k, seg, 4};
+            sdfg_batch_plan *p = nullptr;
+            rc = plan_build(&p, desc, n, check_stride, &c, false);
+            if (rc != SDFG_OK) break;
+            cudaStream_t s = p->cap;
+            rc = plan_run(p, s);
+            if (rc == SDFG_OK) {
+                cudaEventRecord(e0, s);
+                rc = plan_run(p, s);
+                cudaEventRecord(e1, s);
+            }
+            if (rc == SDFG_OK) rc = plan_results(p, tmp.data(), n);
+            float ms = 0.f;
+            if (rc == SDFG_OK) cudaEventElapsedTime(&ms, e0, e1);
+            plan_free(p);
+            if (rc != SDFG_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                winner = c;
+            }
+        }
+        if (rc != SDFG_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SDFG_OK) return rc;
+    autotune_store(-n, -static_cast<int>(area > 2e9 ? 2e9 : area), dtype, winner);
+    *best = winner;
+    return SDFG_OK;
 }
 
 extern "C" int sdfg_test_hook(int hook, long long value) {

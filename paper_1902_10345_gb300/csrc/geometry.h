@@ -3,8 +3,15 @@
 
 namespace sdfg {
 
-constexpr int CHUNK_ROWS = 6;  // rows per TMA box (a multiple of the 3-row register rotation)
-constexpr int STAGES = 4;      // TMA ring depth per warp
+#ifndef SDFG_CHUNK_ROWS
+#define SDFG_CHUNK_ROWS 6
+#endif
+#ifndef SDFG_STAGES
+#define SDFG_STAGES 4
+#endif
+constexpr int CHUNK_ROWS = SDFG_CHUNK_ROWS;  // rows per TMA box (a multiple of the 3-row register rotation)
+constexpr int STAGES = SDFG_STAGES;          // TMA ring depth per warp
+static_assert(CHUNK_ROWS % 3 == 0, "chunks are whole turns of the 3-row rotation");
 constexpr int MAX_WARPS = 16;  // warps per CTA upper bound
 
 // Codes a kernel writes to the per-device error word (first writer wins).

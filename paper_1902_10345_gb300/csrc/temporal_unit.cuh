@@ -10,7 +10,8 @@
 //   Vectorization  -- each lane holds V consecutive columns (16-byte accesses
 //                     for FP32/FP64, 8-byte for BF16);
 //   StateFusion /
-//   MapToForLoop   -- K timestep-states are fused: the warp streams down its
+//   MapToForLoop   -- K timestep-states are fused (in FP32 registers; a BF16
+//                     grid is rounded to BF16 when a pass stores it): the warp streams down its
 //                     column strip and keeps, for every fused level l < K, the
 //                     three most recent rows of level l in registers.  A new
 //                     level-0 row from shared memory lets level 0 produce one
@@ -80,18 +81,6 @@ __device__ __forceinline__ void level_row(double (&o)[V], const double (&n)[V], 
 #pragma unroll
         for (int e = 0; e < V; ++e)
             if ((colmask >> e) & 1u) o[e] = c[e];
-    }
-}
-
-template <class ST, int V>
-__device__ __forceinline__ void storage_round(typename Store<ST>::CT (&o)[V]) {
-    if constexpr (sizeof(ST) == 2) {
-#pragma unroll
-        for (int e = 0; e < V; e += 2) {
-            const float2 f = __bfloat1622float2(__floats2bfloat162_rn(o[e], o[e + 1]));
-            o[e] = f.x;
-            o[e + 1] = f.y;
-        }
     }
 }
 
@@ -195,7 +184,6 @@ struct UnitPipe {
                     for (int e = 0; e < V; ++e) o[e] = b[l][SC][e];
                 }
             }
-            storage_round<ST, V>(o);
             if (RES && l == 0 && (res_flags & 1)) {
                 const int row = r - 1;
                 if (row >= y0 && row < y1) accumulate(g_ref, o, b[0][SC]);
@@ -214,14 +202,13 @@ struct UnitPipe {
     }
 
     // `out` points at output row r0-K (it is only dereferenced for rows the
-    // unit owns).
+    // unit owns).  The chunk is CHUNK_ROWS/3 turns of one 3-row body: a
+    // small hot loop (instruction cache).
     template <bool SLOW>
     __device__ __forceinline__ void chunk_body(int r0, const ST *src, ST *out) {
-        static_assert(CHUNK_ROWS == 6, "chunk body is written for 6 rows");
         const size_t ldr = static_cast<size_t>(ld);
-        // two turns of one 3-row body: a small hot loop (instruction cache)
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < CHUNK_ROWS / 3; ++h) {
             step<0, SLOW>(r0 + 0, src + 0 * W, out);
             step<1, SLOW>(r0 + 1, src + 1 * W, out + ldr);
             step<2, SLOW>(r0 + 2, src + 2 * W, out + 2 * ldr);

@@ -97,6 +97,33 @@ def sinusoid_field(n: int, seed: int = 0, modes: int = 8, k_max: int = 64, noise
     return f
 
 
+def sinusoid_field_device(n: int, seed: int = 0, modes: int = 8, k_max: int = 64, noise: float = 0.05,
+                          device="cuda"):
+    """The sinusoid field of ``sinusoid_field`` built on a torch device (for
+    large n).  The random parameters come from the same numpy stream in the
+    same order; the noise is drawn by numpy per row block so host memory stays
+    bounded.  Values agree with ``sinusoid_field`` up to last-bit differences
+    of the two libraries' sin/cos."""
+    import torch
+    r = rng_for(seed)
+    kx = r.integers(1, k_max + 1, size=modes)
+    ky = r.integers(1, k_max + 1, size=modes)
+    phi = r.uniform(0.0, 2.0 * math.pi, size=modes)
+    w = r.uniform(0.0, 1.0, size=modes)
+    a = 0.5 * w / w.sum()
+    x = torch.arange(n, dtype=torch.float64, device=device) / n
+    f = torch.full((n, n), 0.5, dtype=torch.float64, device=device)
+    for m in range(modes):
+        ax = 2.0 * math.pi * float(kx[m]) * x
+        ay = 2.0 * math.pi * float(ky[m]) * x + float(phi[m])
+        f += float(a[m]) * (torch.outer(torch.cos(ay), torch.sin(ax)) + torch.outer(torch.sin(ay), torch.cos(ax)))
+    block = max(1, (1 << 24) // n)
+    for i0 in range(0, n, block):
+        i1 = min(n, i0 + block)
+        f[i0:i1] += torch.from_numpy(r.uniform(-noise, noise, size=(i1 - i0, n))).to(device)
+    return f
+
+
 @dataclasses.dataclass
 class Request:
     rows: int
@@ -133,6 +160,23 @@ def laplace_request_grid(req: Request, noise: float = 1e-3) -> np.ndarray:
     g = x * x - y * y + r.uniform(-noise, noise, size=(R, C))
     g[1:-1, 1:-1] = 0.0
     return g
+
+
+def laplace_request_grid_device(req: Request, noise: float = 1e-3, device="cuda", dtype=None):
+    """``laplace_request_grid`` built on a torch device.  The noise is drawn
+    by numpy for the whole grid in the same order, so the boundary values
+    match the host version exactly; the interior is zero."""
+    import torch
+    R, C = req.rows, req.cols
+    r = rng_for(req.seed)
+    eta = r.uniform(-noise, noise, size=(R, C))
+    ring = np.zeros((R, C))
+    ring[0, :], ring[-1, :], ring[:, 0], ring[:, -1] = eta[0, :], eta[-1, :], eta[:, 0], eta[:, -1]
+    y = (torch.arange(R, dtype=torch.float64, device=device) / max(R - 1, 1))[:, None]
+    x = (torch.arange(C, dtype=torch.float64, device=device) / max(C - 1, 1))[None, :]
+    g = x * x - y * y + torch.from_numpy(ring).to(device)
+    g[1:-1, 1:-1] = 0.0
+    return g if dtype is None else g.to(dtype)
 
 
 def poisson_arrivals(n: int, rate_hz: float, seed: int = 0) -> np.ndarray:

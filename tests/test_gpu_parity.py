@@ -104,10 +104,17 @@ def test_other_dtypes_match_oracle(dt, shape, T):
         err = np.abs(y - want).max()
         assert err <= TOL[dt], (dt, shape, T, c.k, err)
         outs.append(y)
-    for y in outs[1:]:
-        assert np.array_equal(y, outs[0])
     if dt == F64:
+        for y in outs[1:]:
+            assert np.array_equal(y, outs[0])
         assert np.array_equal(outs[0], want), "FP64 path should equal the oracle bit for bit"
+    else:
+        # BF16 rounds when a pass stores: one step per pass for the naive
+        # kernel and k=1, so those two agree bit for bit; the persistent
+        # kernel at the same k agrees with the per-pass kernel bit for bit
+        assert np.array_equal(outs[0], outs[1])
+        y8p = host64(run(x, T, binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=8)))
+        assert np.array_equal(y8p, outs[4])
 
 
 def test_f64_256_grid_T100_bitwise():
@@ -200,7 +207,8 @@ def test_full_size_8192_T1000_windows_and_properties():
     T = 1000
     g = inputs.uniform_grid(R, C, seed=0)
     x = dev(g, F32)
-    y = run(x, T)
+    bench_cfg = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=8, seg_rows=128, warps=4)
+    y = run(x, T, bench_cfg)
     yh = y.cpu().numpy()
     xh = x.cpu().numpy().astype(np.float64)
     for (r0, c0) in [(0, 0), (0, C - 24), (R - 24, 0), (R - 24, C - 24), (4000, 4100), (0, 3000), (5000, C - 24)]:
@@ -210,7 +218,7 @@ def test_full_size_8192_T1000_windows_and_properties():
     # discrete maximum principle
     assert yh.min() >= xh.min() - 1e-6 and yh.max() <= xh.max() + 1e-6
     # transpose symmetry, bit for bit
-    yt = run(x.t().contiguous(), T)
+    yt = run(x.t().contiguous(), T, bench_cfg)
     assert torch.equal(yt.t(), y)
     # boundary ring untouched
     assert torch.equal(y[0], x[0]) and torch.equal(y[-1], x[-1])
