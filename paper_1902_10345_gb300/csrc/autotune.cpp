@@ -106,12 +106,15 @@ extern "C" int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *
     const long long Tp = std::min<long long>(T, 64);
     const int ks[] = {2, 4, 8};
     const int kernels[] = {SDFG_KERNEL_TEMPORAL, SDFG_KERNEL_PERSISTENT};
-    const int segs_c[] = {96, 128, 192};
+    // short segments give small grids enough units to fill the GPU; tall ones
+    // cut the halo rows of large grids
+    const int segs_c[] = {24, 48, 96, 128, 192};
     float best_ms = 1e30f;
     sdfg_config winner = {SDFG_KERNEL_TEMPORAL, default_depth(dtype), 0, 4};
     for (int k : ks) {
         for (int kern : kernels) {
             for (int sr : segs_c) {
+                if (sr > rows) continue;
                 sdfg_config c = {kern, k, sr, 4};
                 // warm-up, then timed
                 rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);

@@ -1,6 +1,9 @@
 // The temporal-blocked work unit: one warp advances one tile of the grid by
 // K timesteps in a single pass over HBM.
 //
+// FP32 arithmetic reassociates the 5-point sum and applies 0.2^K once per pass
+// (see level_sum); FP64 keeps the exact order 0.2 * (c + ((n + s) + (w + e))).
+//
 // Paper mapping (App. B transformations, applied by hand):
 //   MapTiling      -- the interior map is cut into strips of `wout` columns and
 //                     segments of `H` rows; one warp owns one (strip, segment);
@@ -66,6 +69,51 @@ __device__ __forceinline__ void level_row(float (&o)[V], const float (&n)[V], co
     }
 }
 
+// FP32 arithmetic (FP32 and BF16 storage): a fused level carries the UNSCALED
+// 5-point sum, so interior values at level l are 5^l times the state and the
+// factor 0.2^K is applied once, at the last level of the pass.  The row sum
+// shares horizontal pairs: Q = u0 + u1 serves H0 = w + Q and H1 = Q + u2, so
+// the 5-point sum costs 3.5 adds per point (n + s, H, H + (n + s)) and no
+// multiply.  Boundary cells keep their unscaled value b at every level; a
+// neighbour reads it as 5^l * b (`lscale`), and the last level copies b, so
+// the Dirichlet ring is stored exactly.
+template <int V, bool COLCHK>
+__device__ __forceinline__ void level_sum(float (&o)[V], const float (&n)[V], const float (&c)[V],
+                                          const float (&s)[V], unsigned colmask, float lscale) {
+    static_assert(V % 2 == 0, "pairs of columns");
+    float cc[V];  // the centre row as its neighbours see it
+#pragma unroll
+    for (int e = 0; e < V; ++e) cc[e] = (COLCHK && ((colmask >> e) & 1u)) ? __fmul_rn(c[e], lscale) : c[e];
+    const float left = __shfl_up_sync(FULL_MASK, cc[V - 1], 1);
+    const float right = __shfl_down_sync(FULL_MASK, cc[0], 1);
+    float h[V];
+#pragma unroll
+    for (int p = 0; p < V / 2; ++p) {
+        const float q = __fadd_rn(cc[2 * p], cc[2 * p + 1]);
+        const float w = (p == 0) ? left : cc[2 * p - 1];
+        const float ea = (2 * p + 2 == V) ? right : cc[2 * p + 2];
+        h[2 * p] = __fadd_rn(w, q);
+        h[2 * p + 1] = __fadd_rn(q, ea);
+    }
+#pragma unroll
+    for (int p = 0; p < V / 2; ++p) {
+        const float2 ns = __fadd2_rn(make_float2(n[2 * p], n[2 * p + 1]), make_float2(s[2 * p], s[2 * p + 1]));
+        const float2 r = __fadd2_rn(make_float2(h[2 * p], h[2 * p + 1]), ns);
+        o[2 * p] = r.x;
+        o[2 * p + 1] = r.y;
+    }
+    if (COLCHK) {
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+            if ((colmask >> e) & 1u) o[e] = c[e];
+    }
+}
+
+// 0.2^k in double, for the hi/lo split of the last level's scale factor.
+__host__ __device__ constexpr double pow_fifth(int k) { return k <= 0 ? 1.0 : 0.2 * pow_fifth(k - 1); }
+// 5^k (exact in FP32 for k <= 10).
+__host__ __device__ constexpr float pow_five(int k) { return k <= 0 ? 1.0f : 5.0f * pow_five(k - 1); }
+
 template <int V, bool COLCHK>
 __device__ __forceinline__ void level_row(double (&o)[V], const double (&n)[V], const double (&c)[V],
                                           const double (&s)[V], unsigned colmask) {
@@ -103,7 +151,7 @@ __device__ __noinline__ inline bool drain_after_timeout(uint64_t *bars, uint32_t
 // depends on level l-1 of rows i-1..i+1).  Chunks away from the grid's top and
 // bottom rows and inside the unit's output rows take the FAST body, with no
 // boundary or range test at all.
-template <class ST, int V, int K, bool COLCHK, bool RES>
+template <class ST, int V, int K, bool COLCHK, bool RES, bool EXACT>
 struct UnitPipe {
     using CT = typename Store<ST>::CT;
     static constexpr int W = 32 * V;
@@ -167,6 +215,9 @@ struct UnitPipe {
         constexpr int SN = (PH + 1) % 3;  // slot of the north row
         constexpr int SC = (PH + 2) % 3;  // slot of the centre row
         constexpr int SS = PH;            // slot of the south (newest) row
+        // units away from the boundary ring reassociate (see level_sum); a unit
+        // that holds a boundary row or column keeps the exact order throughout
+        constexpr bool SCALED = sizeof(CT) == 4 && !EXACT;
         {
             CT tmp[V];
             VecIO<ST, V>::load(tmp, src);
@@ -176,22 +227,53 @@ struct UnitPipe {
 #pragma unroll
         for (int l = 0; l < K; ++l) {
             CT o[V];
-            level_row<V, COLCHK>(o, b[l][SN], b[l][SC], b[l][SS], colmask);
-            if (SLOW) {
-                const int rc = r - l - 1;  // row index of this level's centre
-                if (rc <= 0 || rc >= R - 1) {
+            const int rc = r - l - 1;  // row index of this level's centre
+            if constexpr (SCALED) {
+                const float LS = 1.0f;  // (no boundary cell inside a scaled unit)
+                // no boundary row or column reaches this unit: one fast sum
+                level_sum<V, false>(o, b[l][SN], b[l][SC], b[l][SS], colmask, LS);
+                if (l == K - 1) {
+                    // the pass's scale factor 0.2^K, split hi + lo so the product is
+                    // rounded once from a ~48-bit factor
+                    constexpr double F = pow_fifth(K);
+                    constexpr float FHI = static_cast<float>(F);
+                    constexpr float FLO = static_cast<float>(F - static_cast<double>(FHI));
 #pragma unroll
-                    for (int e = 0; e < V; ++e) o[e] = b[l][SC][e];
+                    for (int p = 0; p < V / 2; ++p) {
+                        const float2 u = make_float2(o[2 * p], o[2 * p + 1]);
+                        const float2 t = __fmul2_rn(u, make_float2(FLO, FLO));
+                        const float2 f = __ffma2_rn(u, make_float2(FHI, FHI), t);
+                        o[2 * p] = f.x;
+                        o[2 * p + 1] = f.y;
+                    }
                 }
+            } else {
+                level_row<V, COLCHK>(o, b[l][SN], b[l][SC], b[l][SS], colmask);
+            }
+            if (!SCALED && SLOW && (rc <= 0 || rc >= R - 1)) {
+                // the boundary ring (and rows outside the grid) keep their value
+#pragma unroll
+                for (int e = 0; e < V; ++e) o[e] = b[l][SC][e];
             }
             if (RES && l == 0 && (res_flags & 1)) {
                 const int row = r - 1;
-                if (row >= y0 && row < y1) accumulate(g_ref, o, b[0][SC]);
+                if (row >= y0 && row < y1 && row >= 1 && row <= R - 2) {
+                    CT a1[V];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) a1[e] = (SCALED && K > 1) ? CT(0.2f) * o[e] : o[e];
+                    accumulate(g_ref, a1, b[0][SC]);
+                }
             }
             if (l == K - 1) {
                 const int row = r - K;
                 if (!SLOW || (row >= y0 && row < y1)) {
-                    if (RES && (res_flags & 2)) accumulate(g_chk, o, b[l][SC]);
+                    if (RES && (res_flags & 2) && row >= 1 && row <= R - 2) {
+                        CT prev[V];
+                        constexpr CT PS = SCALED ? CT(pow_fifth(K - 1)) : CT(1);
+#pragma unroll
+                        for (int e = 0; e < V; ++e) prev[e] = PS * b[l][SC][e];
+                        accumulate(g_chk, o, prev);
+                    }
                     store_row(out, o);
                 }
             } else {
@@ -299,9 +381,9 @@ __device__ __forceinline__ bool run_unit(const void *tmap, ST *dst, const GridGe
 
     bool ok;
     double ar = 0.0, ac = 0.0;
-#define SDFG_RUN_PIPE(CHK, RS)                                                                          \
+#define SDFG_RUN_PIPE(CHK, RS, EX)                                                                          \
     {                                                                                                   \
-        UnitPipe<ST, V, K, CHK, RS> p;                                                                  \
+        UnitPipe<ST, V, K, CHK, RS, EX> p;                                                                  \
         p.tmap = tmap; p.dst = dst; p.ld = g.ld; p.R = g.R; p.C = g.C;                                  \
         p.X = X; p.y0 = y0; p.y1 = y1; p.rb = rb; p.n_steps = n_steps; p.n_chunks = n_chunks;           \
         p.base = chunk_ctr; p.ring = ring; p.bars = bars; p.lane = lane;                                \
@@ -310,10 +392,17 @@ __device__ __forceinline__ bool run_unit(const void *tmap, ST *dst, const GridGe
         ok = p.run();                                                                                   \
         if (RS) { ar = p.acc_ref; ac = p.acc_chk; }                                                     \
     }
+    // rows rb .. y1+K-1 are read: a boundary row is among them in the first
+    // and the last segments
+    const bool rowedge = (rb <= 0) || (y1 + K - 1 >= g.R - 1);
     if (res_flags) {
-        if (colchk) SDFG_RUN_PIPE(true, true) else SDFG_RUN_PIPE(false, true)
+        if (colchk) SDFG_RUN_PIPE(true, true, true)
+        else if (rowedge) SDFG_RUN_PIPE(false, true, true)
+        else SDFG_RUN_PIPE(false, true, false)
     } else {
-        if (colchk) SDFG_RUN_PIPE(true, false) else SDFG_RUN_PIPE(false, false)
+        if (colchk) SDFG_RUN_PIPE(true, false, true)
+        else if (rowedge) SDFG_RUN_PIPE(false, false, true)
+        else SDFG_RUN_PIPE(false, false, false)
     }
 #undef SDFG_RUN_PIPE
     chunk_ctr += static_cast<uint32_t>(n_chunks);

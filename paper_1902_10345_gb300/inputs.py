@@ -150,31 +150,46 @@ def served_requests(n: int = 10000, seed: int = 0, lo: int = 32, hi: int = 4096,
     return reqs
 
 
-def laplace_request_grid(req: Request, noise: float = 1e-3) -> np.ndarray:
-    """Boundary x^2 - y^2 on the unit square (x = j/(C-1), y = i/(R-1)) plus
-    uniform noise of amplitude ``noise``; interior zero."""
+def _ring_noise(req: Request, noise: float):
+    """Boundary noise drawn in a fixed order: top row, bottom row, then the
+    left and right columns without their corners."""
     R, C = req.rows, req.cols
     r = rng_for(req.seed)
+    top = r.uniform(-noise, noise, size=C)
+    bottom = r.uniform(-noise, noise, size=C)
+    left = r.uniform(-noise, noise, size=max(R - 2, 0))
+    right = r.uniform(-noise, noise, size=max(R - 2, 0))
+    return top, bottom, left, right
+
+
+def laplace_request_grid(req: Request, noise: float = 1e-3) -> np.ndarray:
+    """Boundary x^2 - y^2 on the unit square (x = j/(C-1), y = i/(R-1)) plus
+    uniform noise of amplitude ``noise`` on the boundary ring; interior zero."""
+    R, C = req.rows, req.cols
     y = (np.arange(R, dtype=np.float64) / max(R - 1, 1))[:, None]
     x = (np.arange(C, dtype=np.float64) / max(C - 1, 1))[None, :]
-    g = x * x - y * y + r.uniform(-noise, noise, size=(R, C))
+    g = x * x - y * y
+    top, bottom, left, right = _ring_noise(req, noise)
+    g[0, :] += top
+    g[-1, :] += bottom
+    g[1:-1, 0] += left
+    g[1:-1, -1] += right
     g[1:-1, 1:-1] = 0.0
     return g
 
 
 def laplace_request_grid_device(req: Request, noise: float = 1e-3, device="cuda", dtype=None):
-    """``laplace_request_grid`` built on a torch device.  The noise is drawn
-    by numpy for the whole grid in the same order, so the boundary values
-    match the host version exactly; the interior is zero."""
+    """``laplace_request_grid`` built on a torch device (same values)."""
     import torch
     R, C = req.rows, req.cols
-    r = rng_for(req.seed)
-    eta = r.uniform(-noise, noise, size=(R, C))
-    ring = np.zeros((R, C))
-    ring[0, :], ring[-1, :], ring[:, 0], ring[:, -1] = eta[0, :], eta[-1, :], eta[:, 0], eta[:, -1]
     y = (torch.arange(R, dtype=torch.float64, device=device) / max(R - 1, 1))[:, None]
     x = (torch.arange(C, dtype=torch.float64, device=device) / max(C - 1, 1))[None, :]
-    g = x * x - y * y + torch.from_numpy(ring).to(device)
+    g = x * x - y * y
+    top, bottom, left, right = (torch.from_numpy(v).to(device) for v in _ring_noise(req, noise))
+    g[0, :] += top
+    g[-1, :] += bottom
+    g[1:-1, 0] += left
+    g[1:-1, -1] += right
     g[1:-1, 1:-1] = 0.0
     return g if dtype is None else g.to(dtype)
 

@@ -2,8 +2,10 @@
 
 Tolerances (max-abs against the FP64 oracle run on exactly the values the GPU
 received): FP32 storage 1e-4, BF16 storage 2e-2, FP64 1e-12 (and bitwise, the
-order of operations being the same).  All kernels and fused depths evaluate
-every update in the same order, so their results must agree bit for bit.
+order of operations being the same).  FP32 units away from the boundary ring
+reassociate the sum, so FP32 results are bit-identical for equal geometry
+(fused depth k and segment height): the per-pass and persistent kernels must
+agree bit for bit in that case.
 
 Full-size cases (8192^2, T=1000) are checked on light-cone windows: the
 oracle runs on a crop that extends T+1 cells past each window, which fixes the
@@ -65,8 +67,12 @@ def cfg(kernel, k=0, seg_rows=0, warps=0):
     return binding.config(kernel=kernel, k=k, seg_rows=seg_rows, warps=warps)
 
 
+PERSISTENT = binding.SDFG_KERNEL_PERSISTENT
 ALL_CFGS = [cfg(NAIVE)] + [cfg(TEMPORAL, k) for k in (1, 2, 4, 8)] + [cfg(TEMPORAL, 8, seg_rows=16, warps=4),
                                                                      cfg(TEMPORAL, 4, seg_rows=24, warps=2)]
+# (per-pass, persistent) pairs with the same geometry: bit-identical results
+SAME_GEOMETRY = [(cfg(TEMPORAL, 8, seg_rows=24, warps=4), cfg(PERSISTENT, 8, seg_rows=24, warps=4)),
+                 (cfg(TEMPORAL, 4, seg_rows=48, warps=2), cfg(PERSISTENT, 4, seg_rows=48, warps=4))]
 
 
 @pytest.mark.parametrize("shape", [(3, 3), (4, 4), (5, 7), (9, 130), (17, 33), (64, 64), (129, 131), (200, 515),
@@ -77,14 +83,12 @@ def test_f32_matches_oracle_all_kernels(shape, T):
     g = inputs.uniform_grid(R, C, seed=R * 1000 + C)
     x = dev(g, F32)
     want = oracle.jacobi2d(host64(x), T, threads=0)
-    results = []
     for c in ALL_CFGS:
         y = host64(run(x, T, c))
         err = np.abs(y - want).max()
         assert err <= TOL[F32], (shape, T, c.kernel, c.k, err)
-        results.append(y)
-    for y in results[1:]:
-        assert np.array_equal(y, results[0]), "kernels disagree bitwise"
+    for c1, c2 in SAME_GEOMETRY:
+        assert np.array_equal(host64(run(x, T, c1)), host64(run(x, T, c2))), "same geometry, different bits"
     # input untouched
     assert np.array_equal(host64(x), g.astype(np.float32).astype(np.float64))
 
@@ -109,12 +113,10 @@ def test_other_dtypes_match_oracle(dt, shape, T):
             assert np.array_equal(y, outs[0])
         assert np.array_equal(outs[0], want), "FP64 path should equal the oracle bit for bit"
     else:
-        # BF16 rounds when a pass stores: one step per pass for the naive
-        # kernel and k=1, so those two agree bit for bit; the persistent
-        # kernel at the same k agrees with the per-pass kernel bit for bit
-        assert np.array_equal(outs[0], outs[1])
-        y8p = host64(run(x, T, binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=8)))
-        assert np.array_equal(y8p, outs[4])
+        # BF16 rounds when a pass stores; the persistent kernel with the same
+        # geometry as the per-pass kernel agrees bit for bit
+        for c1, c2 in SAME_GEOMETRY:
+            assert np.array_equal(host64(run(x, T, c1)), host64(run(x, T, c2)))
 
 
 def test_f64_256_grid_T100_bitwise():
@@ -217,9 +219,10 @@ def test_full_size_8192_T1000_windows_and_properties():
         assert err <= TOL[F32], (r0, c0, err)
     # discrete maximum principle
     assert yh.min() >= xh.min() - 1e-6 and yh.max() <= xh.max() + 1e-6
-    # transpose symmetry, bit for bit
+    # transpose symmetry (bit for bit in exact arithmetic; the reassociated
+    # FP32 sum makes it hold to the FP32 tolerance)
     yt = run(x.t().contiguous(), T, bench_cfg)
-    assert torch.equal(yt.t(), y)
+    assert (yt.t().double() - y.double()).abs().max().item() <= TOL[F32]
     # boundary ring untouched
     assert torch.equal(y[0], x[0]) and torch.equal(y[-1], x[-1])
     assert torch.equal(y[:, 0], x[:, 0]) and torch.equal(y[:, -1], x[:, -1])
