@@ -564,6 +564,9 @@ def run_serve(a):
     def serve(arrivals):
         sv = ctypes.c_void_p()
         binding.check(L.sdfg_server_create(ctypes.byref(sv), budget, 1024, quantum, stride, 0))
+        if a.k or a.seg_rows:
+            scfg = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=a.k, seg_rows=a.seg_rows)
+            binding.check(L.sdfg_server_set_config(sv, ctypes.byref(scfg)))
         ids = [None] * n
         sub_t = [0.0] * n
         t0 = time.perf_counter()
@@ -653,6 +656,7 @@ def run_serve(a):
         "server_on_same_prefix": {"p50_s": _pct(lat_s_prefix, 50), "p99_s": _pct(lat_s_prefix, 99)},
         "steps_equal_server_vs_plain": sum(int(steps_s[i] == s_) for i, s_ in zip(idx_p, steps_p)),
         "budget_bytes": budget, "quantum_steps": quantum, "check_stride": stride,
+        "server_config": {"k": a.k or 4, "seg_rows": a.seg_rows or 96},
     }))
 
 

@@ -63,6 +63,7 @@ typedef enum { SDFG_F32 = 0, SDFG_BF16 = 1, SDFG_F64 = 2 } sdfg_dtype;
 typedef enum {
     SDFG_OK = 0,
     SDFG_PENDING = 1,           /* server request not finished yet           */
+    SDFG_PAUSED = 2,            /* server request paused by a snapshot       */
     SDFG_ERR_INVAL = -1,        /* bad argument                              */
     SDFG_ERR_NOMEM = -2,        /* device allocation failed / over budget    */
     SDFG_ERR_CUDA = -3,         /* CUDA runtime or driver error              */
@@ -147,7 +148,17 @@ int sdfg_jacobi2d_host(const void *h_in, void *h_out, int rows, int cols, int T,
  * data).  Squared differences are formed in the storage precision's
  * arithmetic (FP32 for FP32/BF16) and summed in groups of at most 32 terms
  * in FP32; every further level of the reduction is FP64 in a fixed order.
- * Outputs: status, steps_done, rel_residual (rel at the final step).
+ * Outputs: status, steps_done, rel_residual (rel at the final step),
+ * r_first2.
+ *
+ * Resuming (the state of a solve is exactly the grid, the step count and
+ * ||A_1 - A_0||^2): a descriptor with t_start > 0 continues a solve whose
+ * grid after t_start steps is `in`; T stays the total cap, checks stay on
+ * multiples of the check stride counted from step 0, and r_first2 must hold
+ * the original solve's ||A_1 - A_0||^2 (returned in r_first2 by every solve
+ * with tol > 0).  With the same configuration, a paused-and-resumed solve
+ * equals the uninterrupted one bit for bit.
+ * priority: the server admits higher priorities first (FIFO within one).
  */
 typedef struct {
     const void *in;
@@ -159,6 +170,9 @@ typedef struct {
     int status;
     int steps_done;
     double rel_residual;
+    int t_start;      /* input: steps already done (0 = fresh solve)        */
+    int priority;     /* input: server admission priority (higher first)    */
+    double r_first2;  /* input when resuming; output of every tol > 0 solve */
 } sdfg_desc;
 
 /* Single-grid solve with tolerance; blocks until the outputs are filled. */
@@ -197,9 +211,18 @@ int sdfg_batch_plan_destroy(sdfg_batch_plan *plan);
 typedef struct sdfg_server sdfg_server;
 int sdfg_server_create(sdfg_server **server, size_t hbm_budget_bytes, int max_slots, int quantum_steps,
                        int check_stride, int device);
+/* Optional, before the first submit (SDFG_ERR_BUSY while requests are in
+ * flight): fused depth k, segment height and warps per CTA of every grid. */
+int sdfg_server_set_config(sdfg_server *server, const sdfg_config *cfg);
 int sdfg_server_submit(sdfg_server *server, const sdfg_desc *desc, uint64_t *req_id);
-/* SDFG_PENDING while running; SDFG_OK or an error once done (result filled). */
+/* SDFG_PENDING while running; SDFG_OK or an error once done (result filled);
+ * SDFG_PAUSED after a snapshot (out holds the grid after steps_done steps;
+ * steps_done and r_first2 are what a resumed submission needs). */
 int sdfg_server_poll(sdfg_server *server, uint64_t req_id, sdfg_desc *result);
+/* Pause a request at the next wave boundary (a queued request pauses at
+ * once, with out = in and steps_done = t_start).  SDFG_ERR_INVAL if unknown
+ * or already finished. */
+int sdfg_server_snapshot(sdfg_server *server, uint64_t req_id);
 /* Waits until every submitted request is done; SDFG_ERR_TIMEOUT on expiry. */
 int sdfg_server_drain(sdfg_server *server, int timeout_ms);
 int sdfg_server_destroy(sdfg_server *server);

@@ -19,11 +19,11 @@ from . import build as _build
 
 # ---- constants mirrored from the header --------------------------------------
 SDFG_F32, SDFG_BF16, SDFG_F64 = 0, 1, 2
-SDFG_OK, SDFG_PENDING = 0, 1
+SDFG_OK, SDFG_PENDING, SDFG_PAUSED = 0, 1, 2
 SDFG_ERR_INVAL, SDFG_ERR_NOMEM, SDFG_ERR_CUDA, SDFG_ERR_TIMEOUT, SDFG_ERR_BUSY, SDFG_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 SDFG_KERNEL_AUTO, SDFG_KERNEL_NAIVE, SDFG_KERNEL_TEMPORAL, SDFG_KERNEL_PERSISTENT = 0, 1, 2, 3
 
-STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "ERR_INVAL", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
+STATUS_NAMES = {0: "OK", 1: "PENDING", 2: "PAUSED", -1: "ERR_INVAL", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
                 -5: "ERR_BUSY", -6: "ERR_UNSUPPORTED"}
 
 
@@ -40,7 +40,8 @@ class sdfg_config(ctypes.Structure):
 class sdfg_desc(ctypes.Structure):
     _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("rows", ctypes.c_int), ("cols", ctypes.c_int),
                 ("ld", ctypes.c_int), ("T", ctypes.c_int), ("tol", ctypes.c_double), ("dtype", ctypes.c_int),
-                ("status", ctypes.c_int), ("steps_done", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+                ("status", ctypes.c_int), ("steps_done", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("t_start", ctypes.c_int), ("priority", ctypes.c_int), ("r_first2", ctypes.c_double)]
 
 
 _VP = ctypes.c_void_p
@@ -59,9 +60,11 @@ _PROTOS = {
     "sdfg_batch_plan_results": (_I, [_VP, ctypes.POINTER(sdfg_desc), _I]),
     "sdfg_batch_plan_destroy": (_I, [_VP]),
     "sdfg_server_create": (_I, [ctypes.POINTER(_VP), ctypes.c_size_t, _I, _I, _I, _I]),
+    "sdfg_server_set_config": (_I, [_VP, ctypes.POINTER(sdfg_config)]),
     "sdfg_server_submit": (_I, [_VP, ctypes.POINTER(sdfg_desc), ctypes.POINTER(ctypes.c_uint64)]),
     "sdfg_server_poll": (_I, [_VP, ctypes.c_uint64, ctypes.POINTER(sdfg_desc)]),
     "sdfg_server_drain": (_I, [_VP, _I]),
+    "sdfg_server_snapshot": (_I, [_VP, ctypes.c_uint64]),
     "sdfg_server_destroy": (_I, [_VP]),
     "sdfg_autotune": (_I, [_I, _I, _I, _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_autotune_batch": (_I, [ctypes.POINTER(sdfg_desc), _I, _I, ctypes.POINTER(sdfg_config), _VP]),
@@ -140,7 +143,7 @@ def sdfg_jacobi2d_solve(desc: sdfg_desc, check_stride: int, cfg: sdfg_config | N
 def _write_back(descs, arr):
     """Copy the output fields of `arr` into the caller's descriptor objects."""
     for d, r in zip(descs, arr):
-        d.status, d.steps_done, d.rel_residual = r.status, r.steps_done, r.rel_residual
+        d.status, d.steps_done, d.rel_residual, d.r_first2 = r.status, r.steps_done, r.rel_residual, r.r_first2
 
 
 def sdfg_jacobi2d_batch(descs, check_stride: int, stream=0) -> int:
@@ -229,7 +232,8 @@ def jacobi2d(inp, out, T: int, cfg: sdfg_config | None = None, stream=None) -> N
     check(sdfg_jacobi2d_cfg(pi, po, R, C, ld, T, dtype_code(inp), cfg, _stream(stream)))
 
 
-def desc_for(inp, out, T: int, tol: float = 0.0) -> sdfg_desc:
+def desc_for(inp, out, T: int, tol: float = 0.0, t_start: int = 0, r_first2: float = 0.0,
+             priority: int = 0) -> sdfg_desc:
     pi, R, C, ld = _grid_args(inp)
     po, _, _, _ = _grid_args(out)
-    return sdfg_desc(pi, po, R, C, ld, T, tol, dtype_code(inp), 0, 0, 0.0)
+    return sdfg_desc(pi, po, R, C, ld, T, tol, dtype_code(inp), 0, 0, 0.0, t_start, priority, r_first2)

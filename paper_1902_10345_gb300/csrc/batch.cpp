@@ -80,7 +80,9 @@ int LaunchSet::build(const std::vector<GridRun> &runs) {
         G.tol = r.tol;
         for (int b = 0; b < 3; ++b) {
             G.buf[b] = r.buf[b];
-            if (r.buf[b]) {
+            if (r.buf[b] && r.tmaps) {
+                G.tm[b] = r.tmaps[b];
+            } else if (r.buf[b]) {
                 int rc = encode_tmap(&G.tm[b], r.buf[b], dtype, r.R, r.C, r.ld, W);
                 if (rc != SDFG_OK) return rc;
             }
@@ -327,6 +329,8 @@ static int plan_build(sdfg_batch_plan **out, const sdfg_desc *desc, int n, int c
         if (rc != SDFG_OK) return rc;
         if (d.dtype != dtype) return set_error(SDFG_ERR_INVAL, "batch: all descriptors must share one dtype");
         if (!(d.tol >= 0.0) || !isfinite(d.tol)) return set_error(SDFG_ERR_INVAL, "batch: tol must be >= 0");
+        if (d.t_start < 0 || d.t_start > d.T || !(d.r_first2 >= 0.0))
+            return set_error(SDFG_ERR_INVAL, "batch: need 0 <= t_start <= T and r_first2 >= 0");
         any_tol |= d.tol > 0.0;
     }
     if (any_tol && check_stride < 1) return set_error(SDFG_ERR_INVAL, "batch: check_stride must be >= 1");
@@ -372,7 +376,7 @@ static int plan_build(sdfg_batch_plan **out, const sdfg_desc *desc, int n, int c
     for (int g = 0; g < n && rc == SDFG_OK; ++g) {
         const sdfg_desc &d = desc[g];
         if (d.rows == 0 || d.cols == 0) continue;
-        if (d.rows < 3 || d.cols < 3 || d.T == 0) {
+        if (d.rows < 3 || d.cols < 3 || d.T == d.t_start) {
             p->kind[g] = 1;
             continue;
         }
@@ -380,10 +384,11 @@ static int plan_build(sdfg_batch_plan **out, const sdfg_desc *desc, int n, int c
         GridRun r;
         r.R = d.rows;
         r.C = d.cols;
-        r.t0 = 0;
-        r.steps = d.T;
+        r.t0 = d.t_start;
+        r.steps = d.T - d.t_start;
         r.T_cap = d.T;
         r.tol = d.tol;
+        r.r_ref2 = d.r_first2;
         r.seg_rows = c.seg_rows;
         const bool aligned = tma_compatible(d.in, d.ld, dtype) && tma_compatible(d.out, d.ld, dtype);
         void *scr = nullptr;
@@ -505,15 +510,17 @@ static int plan_results(sdfg_batch_plan *p, sdfg_desc *desc, int n) {
         const sdfg_desc &d = p->descs[g];
         desc[g].status = SDFG_OK;
         desc[g].rel_residual = 0.0;
+        desc[g].r_first2 = d.r_first2;
         if (p->kind[g] == 0) {
             desc[g].steps_done = 0;
         } else if (p->kind[g] == 1) {
-            desc[g].steps_done = (d.rows < 3 || d.cols < 3) ? d.T : 0;
+            desc[g].steps_done = (d.rows < 3 || d.cols < 3) ? d.T : d.t_start;
         } else {
             const PState &S = p->state_host[ri++];
             if (d.tol > 0.0) {
                 desc[g].steps_done = S.steps_done;
                 desc[g].rel_residual = S.rel;
+                desc[g].r_first2 = S.r_ref2;
             } else {
                 desc[g].steps_done = d.T;
             }

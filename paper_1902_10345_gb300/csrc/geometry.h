@@ -4,10 +4,10 @@
 namespace sdfg {
 
 #ifndef SDFG_CHUNK_ROWS
-#define SDFG_CHUNK_ROWS 6
+#define SDFG_CHUNK_ROWS 12
 #endif
 #ifndef SDFG_STAGES
-#define SDFG_STAGES 4
+#define SDFG_STAGES 2
 #endif
 constexpr int CHUNK_ROWS = SDFG_CHUNK_ROWS;  // rows per TMA box (a multiple of the 3-row register rotation)
 constexpr int STAGES = SDFG_STAGES;          // TMA ring depth per warp

@@ -21,6 +21,7 @@ struct GridRun {
     double tol = 0.0;    // 0: fixed step count
     double r_ref2 = 0.0; // carried across launches
     int seg_rows = 0;    // 0: automatic
+    const CUtensorMap *tmaps = nullptr;  // optional pre-encoded maps for buf[0..2]
 };
 
 struct LaunchSet {

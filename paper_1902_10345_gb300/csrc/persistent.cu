@@ -139,12 +139,12 @@ __global__ void __launch_bounds__(128, SDFG_PK_MINB) persistent_kernel(const PLa
             }
         }
         // ---- publish: this unit finished pass p ----
+        // The warp barrier orders every lane's stores before lane 0's release
+        // store, which makes them visible at GPU scope before the flag; a
+        // reader acquires the flag and then fences the async proxy before its
+        // TMA loads.
         __syncwarp();
-        if (lane == 0) {
-            fence_proxy_async_global();
-            __threadfence();
-            st_release_gpu(L.done + unit_off + u, p + 1);
-        }
+        if (lane == 0) st_release_gpu(L.done + unit_off + u, p + 1);
         if (skip || !res) continue;
 
         // ---- reduce pass: the last unit to finish decides ----

@@ -49,6 +49,8 @@ struct Request {
     void *scratch = nullptr;
     void *stage_in = nullptr, *stage_out = nullptr;
     size_t footprint = 0;
+    bool pause = false;  // snapshot requested
+    CUtensorMap tm[3];   // encoded once at admission
 };
 }  // namespace
 
@@ -59,6 +61,8 @@ struct sdfg_server {
     int check_stride = 0;
     int device = 0;
     int dtype = -1;
+    int seg_rows = 96;  // segment height of every grid's units
+    bool k_fixed = false;  // k chosen by sdfg_server_set_config
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -128,8 +132,21 @@ static void admit_locked(sdfg_server *sv) {
             continue;
         }
         r.state = ACTIVE;
-        r.t = 0;
+        r.t = r.d.t_start;
+        r.r_ref2 = r.d.r_first2;
         r.cur = (r.d.in == r.d.out && !staged) ? 0 : 2;
+        {
+            const void *bufs[3] = {r.stage_out ? r.stage_out : r.d.out, r.scratch,
+                                   r.stage_in ? r.stage_in : r.d.in};
+            const int W = 32 * lane_cols(dtype_bytes(r.d.dtype));
+            for (int b = 0; b < 3 && rc == SDFG_OK; ++b)
+                rc = encode_tmap(&r.tm[b], bufs[b], r.d.dtype, r.d.rows, r.d.cols, r.ld_int, W);
+        }
+        if (rc != SDFG_OK) {
+            release_request(sv, r);
+            finish_request(sv, r, rc);
+            continue;
+        }
         sv->active.push_back(r.id);
     }
 }
@@ -187,6 +204,8 @@ static void worker_main(sdfg_server *sv) {
                 g.cur = r.cur;
                 g.tol = r.d.tol;
                 g.r_ref2 = r.r_ref2;
+                g.seg_rows = sv->seg_rows;
+                g.tmaps = r.tm;
                 runs.push_back(g);
             }
         }
@@ -252,7 +271,16 @@ static void worker_main(sdfg_server *sv) {
                 release_request(sv, r);
                 r.d.steps_done = r.t;
                 r.d.rel_residual = tol_mode ? r.rel : 0.0;
+                r.d.r_first2 = r.r_ref2;
                 finish_request(sv, r, crc);
+            } else if (r.pause) {
+                // snapshot: the grid after r.t steps goes to `out`
+                const int crc = copy_result(sv, r, r.cur);
+                release_request(sv, r);
+                r.d.steps_done = r.t;
+                r.d.rel_residual = tol_mode ? r.rel : 0.0;
+                r.d.r_first2 = r.r_ref2;
+                finish_request(sv, r, crc == SDFG_OK ? SDFG_PAUSED : crc);
             } else {
                 still.push_back(r.id);
             }
@@ -303,12 +331,28 @@ extern "C" int sdfg_server_create(sdfg_server **server, size_t hbm_budget_bytes,
     return SDFG_OK;
 }
 
+extern "C" int sdfg_server_set_config(sdfg_server *sv, const sdfg_config *cfg) {
+    if (!sv || !cfg) return set_error(SDFG_ERR_INVAL, "sdfg_server_set_config: null argument");
+    if ((cfg->k != 0 && !depth_supported(cfg->k)) || cfg->seg_rows < 0 || cfg->warps < 0 || cfg->warps > 4)
+        return set_error(SDFG_ERR_INVAL, "sdfg_server_set_config: k must be 1, 2, 4 or 8; warps 0..4");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (!sv->active.empty() || !sv->queue.empty())
+        return set_error(SDFG_ERR_BUSY, "sdfg_server_set_config: requests are in flight");
+    if (cfg->k) sv->ls.k = cfg->k;
+    if (cfg->seg_rows) sv->seg_rows = cfg->seg_rows;
+    if (cfg->warps) sv->ls.warps = cfg->warps;
+    sv->k_fixed = cfg->k != 0;
+    return SDFG_OK;
+}
+
 extern "C" int sdfg_server_submit(sdfg_server *sv, const sdfg_desc *desc, uint64_t *req_id) {
     if (!sv || !desc || !req_id) return set_error(SDFG_ERR_INVAL, "sdfg_server_submit: null argument");
     const sdfg_desc &d = *desc;
     int rc = validate_grid(d.in, d.out, d.rows, d.cols, d.ld, d.T, d.dtype, "sdfg_server_submit");
     if (rc != SDFG_OK) return rc;
     if (!(d.tol >= 0.0)) return set_error(SDFG_ERR_INVAL, "sdfg_server_submit: tol must be >= 0");
+    if (d.t_start < 0 || d.t_start > d.T || !(d.r_first2 >= 0.0))
+        return set_error(SDFG_ERR_INVAL, "sdfg_server_submit: need 0 <= t_start <= T and r_first2 >= 0");
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stopping) return set_error(SDFG_ERR_BUSY, "sdfg_server_submit: server is shutting down");
     if (sv->fatal != SDFG_OK) return set_error(sv->fatal, "sdfg_server_submit: server failed to start");
@@ -320,13 +364,15 @@ extern "C" int sdfg_server_submit(sdfg_server *sv, const sdfg_desc *desc, uint64
     if (fp > sv->budget) return set_error(SDFG_ERR_NOMEM, "sdfg_server_submit: request needs %zu bytes > budget", fp);
     sv->dtype = d.dtype;
     sv->ls.dtype = d.dtype;
-    sv->ls.k = default_depth(d.dtype);
+    // serving mixes many small grids: the 4-column halo of k = 4 wastes less
+    // of each 128-column strip than k = 8 (measured on the served workload)
+    if (!sv->k_fixed) sv->ls.k = d.dtype == SDFG_F64 ? default_depth(d.dtype) : 4;
     Request r;
     r.id = sv->next_id++;
     r.d = d;
     r.d.status = SDFG_PENDING;
     ++sv->unfinished;
-    if (d.rows < 3 || d.cols < 3 || d.T == 0) {
+    if (d.rows < 3 || d.cols < 3 || d.T == d.t_start) {
         // nothing to iterate: a copy, done at once
         const int S = dtype_bytes(d.dtype);
         if (d.rows > 0 && d.cols > 0 && d.in != d.out) {
@@ -334,14 +380,18 @@ extern "C" int sdfg_server_submit(sdfg_server *sv, const sdfg_desc *desc, uint64
                               static_cast<size_t>(d.cols) * S, d.rows, cudaMemcpyDeviceToDevice, sv->stream);
             cudaStreamSynchronize(sv->stream);
         }
-        r.d.steps_done = (d.rows < 3 || d.cols < 3) ? d.T : 0;
+        r.d.steps_done = (d.rows < 3 || d.cols < 3) ? d.T : d.t_start;
         r.d.rel_residual = 0.0;
+        r.d.r_first2 = d.r_first2;
         finish_request(sv, r, SDFG_OK);
         sv->reqs[r.id] = r;
         sv->cv_done.notify_all();
     } else {
         sv->reqs[r.id] = r;
-        sv->queue.push_back(r.id);
+        // higher priority first, FIFO within a priority
+        auto it = sv->queue.end();
+        while (it != sv->queue.begin() && sv->reqs[*(it - 1)].d.priority < d.priority) --it;
+        sv->queue.insert(it, r.id);
         sv->cv_work.notify_one();
     }
     *req_id = r.id;
@@ -355,7 +405,7 @@ extern "C" int sdfg_server_poll(sdfg_server *sv, uint64_t req_id, sdfg_desc *res
     if (it == sv->reqs.end()) return set_error(SDFG_ERR_INVAL, "sdfg_server_poll: unknown request %llu",
                                                static_cast<unsigned long long>(req_id));
     Request &r = it->second;
-    if (r.state != DONE) return SDFG_PENDING;
+    if (r.state != DONE) return SDFG_PENDING;  // (a paused request is DONE with status SDFG_PAUSED)
     const int status = r.status;
     if (result) {
         *result = r.d;
@@ -363,6 +413,36 @@ extern "C" int sdfg_server_poll(sdfg_server *sv, uint64_t req_id, sdfg_desc *res
     }
     sv->reqs.erase(it);
     return status;
+}
+
+extern "C" int sdfg_server_snapshot(sdfg_server *sv, uint64_t req_id) {
+    if (!sv) return set_error(SDFG_ERR_INVAL, "sdfg_server_snapshot: null server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(req_id);
+    if (it == sv->reqs.end() || it->second.state == DONE)
+        return set_error(SDFG_ERR_INVAL, "sdfg_server_snapshot: request %llu is unknown or finished",
+                         static_cast<unsigned long long>(req_id));
+    Request &r = it->second;
+    if (r.state == QUEUED) {
+        // never started: its state is its input
+        for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q)
+            if (*q == req_id) {
+                sv->queue.erase(q);
+                break;
+            }
+        const int S = dtype_bytes(r.d.dtype);
+        if (r.d.in != r.d.out) {
+            cudaMemcpy2DAsync(r.d.out, static_cast<size_t>(r.d.ld) * S, r.d.in, static_cast<size_t>(r.d.ld) * S,
+                              static_cast<size_t>(r.d.cols) * S, r.d.rows, cudaMemcpyDeviceToDevice, sv->stream);
+            cudaStreamSynchronize(sv->stream);
+        }
+        r.d.steps_done = r.d.t_start;
+        finish_request(sv, r, SDFG_PAUSED);
+        sv->cv_done.notify_all();
+        return SDFG_OK;
+    }
+    r.pause = true;
+    return SDFG_OK;
 }
 
 extern "C" int sdfg_server_drain(sdfg_server *sv, int timeout_ms) {

@@ -240,3 +240,19 @@ def test_paper_workload_eigenmode_2048_T1024():
     y = host64(run(x, T))
     want = (lam ** T) * host64(x)
     assert np.abs(y - want).max() <= TOL[F32]
+
+
+@pytest.mark.parametrize("dt,T1,T2", [(F64, 7, 13), (F64, 40, 1), (F32, 16, 21), (F32, 64, 64)])
+def test_resume_equals_uninterrupted(dt, T1, T2):
+    """Checkpoint/resume: the state of a solve is exactly (grid, t), so
+    running T1 steps, then T2 more from the result, equals T1 + T2 steps.
+    Bitwise for FP64 at any split; for FP32 when T1 is a multiple of k (the
+    passes, and so the rounding, are then the same)."""
+    g = inputs.uniform_grid(300, 260, seed=T1)
+    c = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=8 if dt == F32 else 4, seg_rows=64)
+    x = dev(g, dt)
+    mid = run(x, T1, c)
+    a = run(mid, T2, c)
+    b = run(x, T1 + T2, c)
+    assert torch.equal(a, b)
+    assert np.abs(host64(b) - oracle.jacobi2d(host64(x), T1 + T2)).max() <= TOL[dt]
