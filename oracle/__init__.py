@@ -6,6 +6,8 @@ this package.  The CUDA library never calls it, and the two share no code:
 this wrapper loads ``jacobi2d_oracle.c`` compiled by gcc with
 ``-O2 -ffp-contract=off`` (no fast-math), nothing else.
 
+``laplace1d`` is the 1-D Laplace program printed in the paper's Fig. 1.
+
 What it computes is the plain definition (paper Sec. 6.1, Jacobi stencil;
 Fig. 1 for the ping-pong state loop; Sec. 3 "State" for the data-dependent
 stop condition); the C file's header spells out the formula and each reading
@@ -68,6 +70,8 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.oracle_jacobi2d_tol.argtypes = [dp, dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double,
                                         ctypes.c_long, ctypes.c_int, lp, dp, dp]
     lib.oracle_jacobi2d_tol.restype = ctypes.c_int
+    lib.oracle_laplace1d.argtypes = [dp, ctypes.c_long, ctypes.c_long]
+    lib.oracle_laplace1d.restype = ctypes.c_int
     lib.oracle_num_threads.argtypes = [ctypes.c_int]
     lib.oracle_num_threads.restype = ctypes.c_int
     return lib
@@ -121,6 +125,19 @@ def jacobi2d_tol(grid, T_cap: int, tol: float, check_stride: int, threads: int =
     if rc != 0:
         raise ValueError(f"oracle_jacobi2d_tol failed with status {rc}")
     return out, int(steps.value), float(rel.value), float(r1.value)
+
+
+def laplace1d(A2, T: int, lib=None) -> np.ndarray:
+    """The paper's Fig. 1 program on a copy of the float64[2, N] array A2:
+    returns the array as the program leaves it after T steps."""
+    lib = lib or _get()
+    a = np.array(A2, dtype=np.float64, copy=True, order="C")
+    if a.ndim != 2 or a.shape[0] != 2:
+        raise ValueError("A must have shape (2, N)")
+    rc = lib.oracle_laplace1d(_dptr(a), a.shape[1], int(T))
+    if rc != 0:
+        raise ValueError(f"oracle_laplace1d failed with status {rc}")
+    return a
 
 
 def jacobi2d_window(grid, T: int, r0: int, r1: int, c0: int, c1: int, threads: int = 1, lib=None) -> np.ndarray:

@@ -226,3 +226,29 @@ int oracle_jacobi2d_tol(const double *in, double *out, long R, long C,
     free(rowsum);
     return ORACLE_OK;
 }
+
+/*
+ * The 1-D Laplace program of the paper's Fig. 1: a float64[2, N] array A is
+ * ping-ponged for T steps,
+ *
+ *   for t in 0..T-1:  for 1 <= i <= N-2:
+ *       A[(t+1) % 2][i] = A[t % 2][i-1]*1 + A[t % 2][i]*(-2) + A[t % 2][i+1]*1
+ *
+ * (the memlet A[t%2, i-1:i+2] times [1, -2, 1], summed left to right).  The
+ * end cells A[r][0] and A[r][N-1] of each row r are never written, so a step
+ * reading row r sees row r's initial ends.  A (2*N doubles, row-major) is
+ * updated in place exactly as the program leaves it.
+ */
+int oracle_laplace1d(double *A, long N, long T)
+{
+    long t, i;
+    if (N < 0 || T < 0 || (N > 0 && !A))
+        return ORACLE_EINVAL;
+    for (t = 0; t < T; ++t) {
+        const double *src = A + (t % 2) * N;
+        double *dst = A + ((t + 1) % 2) * N;
+        for (i = 1; i < N - 1; ++i)
+            dst[i] = (src[i - 1] * 1.0 + src[i] * -2.0) + src[i + 1] * 1.0;
+    }
+    return ORACLE_OK;
+}

@@ -53,3 +53,37 @@ def test_mutant_is_caught(name, tmp_path):
         except AssertionError:
             caught.append(pin.__name__)
     assert caught, f"no pin caught mutant {name}"
+
+
+# ---- the Fig. 1 program (oracle_laplace1d) ----------------------------------------
+from tests import test_oracle_laplace1d as _l1d  # noqa: E402
+
+LAPLACE_PINS = [_l1d.test_hand_steps, _l1d.test_exact_bruteforce, _l1d.test_eigenvector_closed_form,
+                _l1d.test_paper_configuration_runs]
+
+LAPLACE_MUTANTS = {
+    "weight_centre": ("src[i] * -2.0", "src[i] * -1.0"),
+    "weight_sign": ("src[i - 1] * 1.0 + src[i] * -2.0", "src[i - 1] * 1.0 - src[i] * -2.0"),
+    "neighbour_index": ("+ src[i + 1] * 1.0", "+ src[i] * 1.0"),
+    "no_ping_pong": ("double *dst = A + ((t + 1) % 2) * N;", "double *dst = A + (t % 2) * N;"),
+    "ends_written": ("for (i = 1; i < N - 1; ++i)\n            dst[i]", "for (i = 0; i < N - 1; ++i)\n            dst[i]"),
+    "off_by_one_T": ("for (t = 0; t < T; ++t) {\n        const double *src = A + (t % 2) * N;",
+                     "for (t = 1; t < T; ++t) {\n        const double *src = A + (t % 2) * N;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LAPLACE_MUTANTS))
+def test_laplace1d_mutant_is_caught(name, tmp_path):
+    old, new = LAPLACE_MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    path = tmp_path / f"mut_{name}.c"
+    path.write_text(src.replace(old, new, 1))
+    lib = oracle.load_library(oracle.compile_source(str(path), str(tmp_path / f"libmut_{name}.so")))
+    caught = []
+    for pin in LAPLACE_PINS:
+        try:
+            pin(lib)
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, f"no pin caught mutant {name}"
