@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import glob
 import json
+import math
 import os
 import re
 import statistics
@@ -174,9 +175,28 @@ def _oracle_step_seconds(g) -> float:
     t2 = time.perf_counter()
     return max((t2 - t1) - (t1 - t0), 1e-4) / 4
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_oracle_sample(a, target_s: float):
     """Time the FP64 oracle on a bounded sample of the workload (same grid,
-    fewer timesteps, all host threads)."""
+    fewer timesteps): on all host threads, and on one thread for a quarter of
+    the time."""
     import numpy as np
 
     import oracle
@@ -190,9 +210,31 @@ def cpu_oracle_sample(a, target_s: float):
     oracle.jacobi2d(g, T_s, threads=0)
     el = time.perf_counter() - t0
     upd = (a.rows - 2) * (a.cols - 2) * T_s
+    # single thread: a few timesteps (about target_s / 4 of CPU time)
+    T_1 = int(max(1, min(a.T, 0.25 * target_s / (dt * threads))))
+    t0 = time.perf_counter()
+    oracle.jacobi2d(g, T_1, threads=1)
+    el1 = time.perf_counter() - t0
     return {"value": upd / el / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{a.rows}x{a.cols} grid, FP64 oracle, {T_s} of {a.T} timesteps, {threads} host threads, "
-                      f"{el:.1f} s"}
+                      f"{el:.1f} s",
+            "cpu_model": cpu_model(),
+            "single_thread": {"value": (a.rows - 2) * (a.cols - 2) * T_1 / el1 / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": f"{T_1} of {a.T} timesteps, 1 thread, {el1:.1f} s"}}
+
+
+def median_ci95(xs):
+    """Median of xs and a distribution-free 95% confidence interval for it
+    (order statistics at n/2 -+ 1.96 sqrt(n)/2)."""
+    v = sorted(xs)
+    n = len(v)
+    if n == 0:
+        return None, [None, None]
+    med = v[n // 2] if n % 2 else 0.5 * (v[n // 2 - 1] + v[n // 2])
+    half = 1.96 * math.sqrt(n) / 2
+    lo = max(0, int(math.floor(n / 2 - half)) - 1)
+    hi = min(n - 1, int(math.ceil(n / 2 + half)) - 1)
+    return med, [v[lo], v[hi]]
 
 
 # -------------------------------------------------------------- reference ------
@@ -271,17 +313,18 @@ def run_ours(a):
 
     binding.sdfg_stats_reset()
     binding.sdfg_stats_enable(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
     with ClockSampler(local) as clk:
         barrier()
-        e0.record(stream)
-        for _ in range(a.steps):
+        evs[0].record(stream)
+        for i in range(a.steps):
             binding.jacobi2d(x, y, T, cfg)
-        e1.record(stream)
+            evs[i + 1].record(stream)
         barrier()
     binding.sdfg_stats_enable(False)
-    ms = e0.elapsed_time(e1)
+    ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
+    med_ms, ci_ms = median_ci95(step_ms)
     launches = {}
     for fam in ("naive", "temporal", "persistent", "reduce", "copy"):
         launches[fam] = binding.sdfg_stats_get(fam)
@@ -304,7 +347,14 @@ def run_ours(a):
     e2e_s = time.perf_counter() - t0
     e2e_max = max_over_ranks(e2e_s, dist, "cuda")
     e2e_value = aggregate_rate(updates * a.steps, world, e2e_max) / 1e9
-    assert torch.equal(hy.cuda(), y), "end-to-end result differs from the device-resident result"
+    # the host entry point runs the library's default geometry (persistent,
+    # k = 8, 128-row segments): bitwise equal when the timed configuration is
+    # that one; otherwise the unit geometry decides which units keep the exact
+    # summation order, so the two agree to the FP32 parity tolerance
+    if (cfg.kernel, cfg.k, cfg.seg_rows, cfg.warps) == (binding.SDFG_KERNEL_PERSISTENT, 8, 128, 4):
+        assert torch.equal(hy.cuda(), y), "end-to-end result differs from the device-resident result"
+    else:
+        assert (hy.cuda() - y).abs().max().item() <= 1e-4, "end-to-end result differs from the device-resident result"
 
     if rank != 0:
         if dist is not None:
@@ -345,6 +395,8 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": max(3, a.warmup),
         "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
+        "step_ms": {"median": med_ms, "ci95": ci_ms, "min": min(step_ms), "max": max(step_ms),
+                    "median_gupdates": updates / (med_ms / 1e3) / 1e9 if med_ms else None},
         "config": {"workload": workload_name(a), "rows": R, "cols": C, "T": T, "k": k_used,
                    "kernel": a.kernel, "seg_rows": cfg.seg_rows, "warps_per_cta": cfg.warps,
                    "l2": "inputs larger than L2 (two 256 MiB grids), no flush", "parallelism": f"replicas{world}"},

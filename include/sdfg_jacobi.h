@@ -227,6 +227,17 @@ int sdfg_server_snapshot(sdfg_server *server, uint64_t req_id);
 int sdfg_server_drain(sdfg_server *server, int timeout_ms);
 int sdfg_server_destroy(sdfg_server *server);
 
+/*
+ * The 1-D Laplace program printed in the paper's Fig. 1, on a device
+ * float64[2][N] array A (row-major, rows contiguous):
+ *   for t in 0..T-1, 1 <= i <= N-2:
+ *     A[(t+1)%2][i] = A[t%2][i-1]*1 + A[t%2][i]*(-2) + A[t%2][i+1]*1
+ * in that order (FP64, round-to-nearest).  The end cells of each row are never
+ * written.  A is updated in place, both rows, exactly as the program leaves
+ * it; the result is bit-identical to a plain FP64 loop.  Asynchronous.
+ */
+int sdfg_laplace1d(double *A, int N, int T, void *stream);
+
 /* Autotuner: times candidate configurations for this shape and dtype on the
  * calling stream, caches the best by shape class, and returns it. */
 int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *best, void *stream);

@@ -66,6 +66,7 @@ _PROTOS = {
     "sdfg_server_drain": (_I, [_VP, _I]),
     "sdfg_server_snapshot": (_I, [_VP, ctypes.c_uint64]),
     "sdfg_server_destroy": (_I, [_VP]),
+    "sdfg_laplace1d": (_I, [_VP, _I, _I, _VP]),
     "sdfg_autotune": (_I, [_I, _I, _I, _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_autotune_batch": (_I, [ctypes.POINTER(sdfg_desc), _I, _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_stats_enable": (_I, [_I]),
@@ -151,6 +152,10 @@ def sdfg_jacobi2d_batch(descs, check_stride: int, stream=0) -> int:
     rc = lib().sdfg_jacobi2d_batch(arr, len(descs), check_stride, stream)
     _write_back(descs, arr)
     return rc
+
+
+def sdfg_laplace1d(A: int, N: int, T: int, stream: int = 0) -> int:
+    return lib().sdfg_laplace1d(A, N, T, stream)
 
 
 def sdfg_autotune(rows, cols, T, dtype, stream=0) -> sdfg_config:
