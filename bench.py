@@ -210,8 +210,9 @@ def cpu_oracle_sample(a, target_s: float):
     oracle.jacobi2d(g, T_s, threads=0)
     el = time.perf_counter() - t0
     upd = (a.rows - 2) * (a.cols - 2) * T_s
-    # single thread: a few timesteps (about target_s / 4 of CPU time)
-    T_1 = int(max(1, min(a.T, 0.25 * target_s / (dt * threads))))
+    # single thread: a few timesteps, about target_s / 4 of wall time (one
+    # thread takes at most `threads` times the measured all-thread step time)
+    T_1 = int(max(1, min(a.T, 0.25 * target_s / (el / T_s * threads))))
     t0 = time.perf_counter()
     oracle.jacobi2d(g, T_1, threads=1)
     el1 = time.perf_counter() - t0
@@ -347,11 +348,12 @@ def run_ours(a):
     e2e_s = time.perf_counter() - t0
     e2e_max = max_over_ranks(e2e_s, dist, "cuda")
     e2e_value = aggregate_rate(updates * a.steps, world, e2e_max) / 1e9
-    # the host entry point runs the library's default geometry (persistent,
-    # k = 8, 128-row segments): bitwise equal when the timed configuration is
-    # that one; otherwise the unit geometry decides which units keep the exact
-    # summation order, so the two agree to the FP32 parity tolerance
-    if (cfg.kernel, cfg.k, cfg.seg_rows, cfg.warps) == (binding.SDFG_KERNEL_PERSISTENT, 8, 128, 4):
+    # the host entry point runs the library's default geometry (k = 8,
+    # 128-row segments): FP32 results depend only on k and the segment height
+    # (they decide which units keep the exact summation order), so the two are
+    # bitwise equal for that geometry and agree to the FP32 parity tolerance
+    # otherwise
+    if (cfg.k, cfg.seg_rows) == (8, 128):
         assert torch.equal(hy.cuda(), y), "end-to-end result differs from the device-resident result"
     else:
         assert (hy.cuda() - y).abs().max().item() <= 1e-4, "end-to-end result differs from the device-resident result"

@@ -149,6 +149,9 @@ GridGeo plan_geometry(int rows, int cols, int ld, int dtype, int k, int seg_rows
         H = std::max(H, 2 * std::max(k, 1));
         H = std::max(H, 16);
     }
+    // a unit's input rows (k above and below its own) must lie within the
+    // segments next to its own: the persistent kernel waits on those alone
+    H = std::max(H, std::max(k, 1));
     g.H = std::max(1, std::min(H, std::max(rows, 1)));
     g.n_segs = std::max(1, (rows + g.H - 1) / g.H);
     return g;

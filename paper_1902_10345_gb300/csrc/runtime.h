@@ -58,7 +58,7 @@ void scratch_free(void *p, cudaStream_t s);
 
 // ---- planning ----------------------------------------------------------------
 // Geometry of a grid for fused depth k (halo >= k).  seg_rows 0 = automatic,
-// aiming at `target_units` units.
+// aiming at `target_units` units; segments are at least k rows high.
 GridGeo plan_geometry(int rows, int cols, int ld, int dtype, int k, int seg_rows, long long target_units);
 // Pass depths for T steps at main depth k: k, k, ..., then the remainder in
 // powers of two (largest first).
