@@ -36,7 +36,7 @@ constexpr int PASS_REDUCE = PASS_REF | PASS_CHECK | PASS_FINAL;
 
 // Buffers of a grid: 0 = caller's out (or its aligned stand-in), 1 = scratch,
 // 2 = caller's in (or its aligned stand-in).
-struct alignas(64) PGrid {
+struct PGrid {  // (aligned as its CUtensorMap members: 128 bytes)
     CUtensorMap tm[3];
     void *buf[3];
     GridGeo geo;

@@ -151,6 +151,10 @@ __device__ __noinline__ inline bool drain_after_timeout(uint64_t *bars, uint32_t
 // depends on level l-1 of rows i-1..i+1).  Chunks away from the grid's top and
 // bottom rows and inside the unit's output rows take the FAST body, with no
 // boundary or range test at all.
+#ifndef SDFG_SCALED_ONE_BODY
+#define SDFG_SCALED_ONE_BODY 1
+#endif
+
 template <class ST, int V, int K, bool COLCHK, bool RES, bool EXACT>
 struct UnitPipe {
     using CT = typename Store<ST>::CT;
@@ -330,7 +334,12 @@ struct UnitPipe {
                               (r0 + CHUNK_ROWS - K <= y1);
             // pointer arithmetic only: rows before 0 are never dereferenced
             ST *out = dst + (static_cast<ptrdiff_t>(r0) - K) * ld + (X + lane * V);
-            if (fast)
+            // A reassociated unit's boundary-checked body differs from the fast
+            // one only by a store predicate on the row: one body keeps the hot
+            // code small (instruction cache).  Exact-order units keep both:
+            // their checked body tests every level's row.
+            constexpr bool ONE_BODY = SDFG_SCALED_ONE_BODY && sizeof(CT) == 4 && !EXACT;
+            if (fast && !ONE_BODY)
                 chunk_body<false>(r0, src, out);
             else
                 chunk_body<true>(r0, src, out);
