@@ -1,12 +1,16 @@
-"""FP64 CPU oracle for the iterated 5-point Jacobi-2D stencil.
+"""FP64 CPU oracles for the iterated Jacobi stencils (2-D 5-point, 3-D 7-point)
+and the 1-D Laplace program of the paper's Fig. 1.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 ``bench.py``'s CPU-baseline leg (and its ``--impl reference`` arm) may import
 this package.  The CUDA library never calls it, and the two share no code:
-this wrapper loads ``jacobi2d_oracle.c`` compiled by gcc with
-``-O2 -ffp-contract=off`` (no fast-math), nothing else.
+this wrapper loads ``jacobi2d_oracle.c`` and ``jacobi3d_oracle.c``, each
+compiled by gcc with ``-O2 -ffp-contract=off`` (no fast-math), nothing else.
 
 ``laplace1d`` is the 1-D Laplace program printed in the paper's Fig. 1.
+``jacobi3d`` is the same method as the 2-D Jacobi stencil one dimension up
+(7 points, weight 1/7 each, fixed one-cell shell); the C file's header gives
+the formula and its readings.
 
 What it computes is the plain definition (paper Sec. 6.1, Jacobi stencil;
 Fig. 1 for the ping-pong state loop; Sec. 3 "State" for the data-dependent
@@ -19,11 +23,15 @@ depends only on the input within distance T of it.  Running the definition on
 a crop that extends T+1 cells past the window (clamped to the grid) therefore
 gives the window's values exactly, whatever the crop's artificial edge does.
 
-Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+Parity status: the 2-D functions are pinned by ``tests/test_oracle_pins.py``
 (hand-computed 4x4 fixtures, exact rational brute force, closed-form
 eigenmodes, harmonic fixed points, maximum principle, symmetries, semigroup,
-thread-count invariance, closed-form stopping step) and by mutation tests that
-plant mistakes in a copy of the C source and check the pins catch them.
+thread-count invariance, closed-form stopping step), ``laplace1d`` by
+``tests/test_oracle_laplace1d.py`` and ``jacobi3d`` by
+``tests/test_oracle_jacobi3d.py`` (hand-computed 4x4x4 fixtures, closed-form
+eigenmodes, harmonic fixed points, maximum principle, symmetries, semigroup,
+thread-count invariance); mutation tests plant mistakes in a copy of each C
+source and check that the pins catch them.
 """
 from __future__ import annotations
 
@@ -36,10 +44,13 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "jacobi2d_oracle.c")
+_SRC3D = os.path.join(_HERE, "jacobi3d_oracle.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
+_LIB3D_PATH = os.path.join(_BUILD_DIR, "liboracle3d.so")
 _lock = threading.Lock()
 _lib = None
+_lib3d = None
 
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c99"]
 
@@ -54,11 +65,22 @@ def compile_source(src: str, out: str) -> str:
 
 
 def build(force: bool = False) -> str:
-    """Build liboracle.so (only if missing or older than the source)."""
+    """Build liboracle.so and liboracle3d.so (each only if missing or older
+    than its source); returns the 2-D library's path."""
     with _lock:
-        if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-            compile_source(_SRC, _LIB_PATH)
+        for src, lib in ((_SRC, _LIB_PATH), (_SRC3D, _LIB3D_PATH)):
+            if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+                compile_source(src, lib)
     return _LIB_PATH
+
+
+def load_library3d(path: str) -> ctypes.CDLL:
+    lib = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_jacobi3d.argtypes = [dp, dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_long,
+                                    ctypes.c_int]
+    lib.oracle_jacobi3d.restype = ctypes.c_int
+    return lib
 
 
 def load_library(path: str) -> ctypes.CDLL:
@@ -82,6 +104,14 @@ def _get():
     if _lib is None:
         _lib = load_library(build())
     return _lib
+
+
+def _get3d():
+    global _lib3d
+    if _lib3d is None:
+        build()
+        _lib3d = load_library3d(_LIB3D_PATH)
+    return _lib3d
 
 
 def _dptr(a: np.ndarray):
@@ -155,3 +185,32 @@ def jacobi2d_window(grid, T: int, r0: int, r1: int, c0: int, c1: int, threads: i
     cc0, cc1 = max(0, c0 - m), min(C, c1 + m)
     crop = jacobi2d(a[cr0:cr1, cc0:cc1], T, threads=threads, lib=lib)
     return crop[r0 - cr0:r1 - cr0, c0 - cc0:c1 - cc0]
+
+
+def jacobi3d(box, T: int, threads: int = 1, lib=None) -> np.ndarray:
+    """D x R x C box after T timesteps of the 7-point stencil (FP64; the input
+    is converted to FP64 exactly).  threads 0 = the OpenMP default."""
+    lib = lib or _get3d()
+    a = np.ascontiguousarray(np.asarray(box, dtype=np.float64))
+    if a.ndim != 3:
+        raise ValueError("box must be 3-D")
+    out = np.empty_like(a)
+    rc = lib.oracle_jacobi3d(_dptr(a), _dptr(out), a.shape[0], a.shape[1], a.shape[2], int(T), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_jacobi3d failed with status {rc}")
+    return out
+
+
+def jacobi3d_window(box, T: int, lo, hi, threads: int = 1, lib=None) -> np.ndarray:
+    """box[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]] after T steps, from a
+    light-cone crop that extends T+1 cells past the window along each axis
+    (clamped to the box): exact, as in ``jacobi2d_window``."""
+    a = np.asarray(box)
+    m = int(T) + 1
+    cl = [max(0, int(l) - m) for l in lo]
+    ch = [min(n, int(h) + m) for n, h in zip(a.shape, hi)]
+    for l, h, n in zip(lo, hi, a.shape):
+        if not 0 <= l <= h <= n:
+            raise ValueError("window out of range")
+    crop = jacobi3d(a[cl[0]:ch[0], cl[1]:ch[1], cl[2]:ch[2]], T, threads=threads, lib=lib)
+    return crop[lo[0] - cl[0]:hi[0] - cl[0], lo[1] - cl[1]:hi[1] - cl[1], lo[2] - cl[2]:hi[2] - cl[2]]

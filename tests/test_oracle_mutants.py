@@ -87,3 +87,39 @@ def test_laplace1d_mutant_is_caught(name, tmp_path):
         except AssertionError:
             caught.append(pin.__name__)
     assert caught, f"no pin caught mutant {name}"
+
+
+# ---- the 3-D 7-point oracle (oracle_jacobi3d) --------------------------------------
+from tests import test_oracle_jacobi3d as _j3d  # noqa: E402
+
+SRC3D = os.path.join(os.path.dirname(oracle.__file__), "jacobi3d_oracle.c")
+
+JACOBI3D_MUTANTS = {
+    "weight": ("static const double ONE_SEVENTH = 1.0 / 7.0;", "static const double ONE_SEVENTH = 1.0 / 6.0;"),
+    "drop_planes": ("double sum = centre + ((ns + we) + ud);", "double sum = centre + (ns + we);"),
+    "drop_centre": ("double sum = centre + ((ns + we) + ud);", "double sum = (ns + we) + ud;"),
+    "plane_stride": ("double ud = row[j - P] + row[j + P];", "double ud = row[j - P] + row[j + C];"),
+    "row_index": ("double ns = row[j - C] + row[j + C];", "double ns = row[j - C] + row[j - C];"),
+    "sign_west": ("double we = row[j - 1] + row[j + 1];", "double we = row[j + 1] - row[j - 1];"),
+    "last_row_skipped": ("for (i = 1; i < R - 1; ++i) {", "for (i = 1; i < R - 2; ++i) {"),
+    "in_place": ("        oracle3d_step(A, B, D, R, C, nth);", "        oracle3d_step(A, A, D, R, C, nth);"),
+    "off_by_one_T": ("for (t = 1; t <= T; ++t) {", "for (t = 2; t <= T; ++t) {"),
+    "shell_written": ("dst[j] = ONE_SEVENTH * sum;", "dst[j] = ONE_SEVENTH * sum;\n                if (j == 1) dst[0] = dst[1];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(JACOBI3D_MUTANTS))
+def test_jacobi3d_mutant_is_caught(name, tmp_path):
+    old, new = JACOBI3D_MUTANTS[name]
+    src = open(SRC3D).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    path = tmp_path / f"mut3d_{name}.c"
+    path.write_text(src.replace(old, new, 1))
+    lib = oracle.load_library3d(oracle.compile_source(str(path), str(tmp_path / f"libmut3d_{name}.so")))
+    caught = []
+    for pin in _j3d.ALL_PINS:
+        try:
+            pin(lib)
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, f"no pin caught mutant {name}"
