@@ -50,9 +50,12 @@ def parse():
     p.add_argument("--kernel", choices=["persistent", "temporal"], default="persistent")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
-    p.add_argument("--workload", choices=["single", "batch", "precision", "serve", "paper"], default="single",
+    p.add_argument("--workload", choices=["single", "batch", "precision", "serve", "paper", "3d"], default="single",
                    help="single: 8192^2 FP32 T=1000 (the default line); batch: 512 uneven grids in one "
-                        "persistent launch; precision: 4 x 16384^2 T=500 FP32 and BF16; serve: Laplace requests")
+                        "persistent launch; precision: 4 x 16384^2 T=500 FP32 and BF16; serve: Laplace requests; "
+                        "3d: the 7-point stencil on a 512^3 FP32 box, T=100")
+    p.add_argument("--size3d", type=int, default=512, help="3d: box edge")
+    p.add_argument("--T3d", type=int, default=100, help="3d: timesteps")
     p.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
     p.add_argument("--rho", type=float, default=0.9, help="serve: arrival rate as a fraction of served capacity")
     p.add_argument("--plain-seconds", type=float, default=120.0,
@@ -327,7 +330,7 @@ def run_ours(a):
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
     med_ms, ci_ms = median_ci95(step_ms)
     launches = {}
-    for fam in ("naive", "temporal", "persistent", "reduce", "copy"):
+    for fam in ("naive", "temporal", "persistent", "reduce", "copy", "stencil3d"):
         launches[fam] = binding.sdfg_stats_get(fam)
     binding.sdfg_stats_reset()
     binding.check(binding.sdfg_device_error(True))
@@ -585,6 +588,101 @@ def run_paper(a):
                       "note": "paper's own figure for this workload is in a lost plot (P100); context only"}))
 
 
+# ---------------------------------------------------------------------- 3-D -------
+def run_3d(a):
+    """The 7-point stencil on an n^3 FP32 box (uniform [0,1) from seed 0,
+    shell included), T timesteps, one launch per step; inputs (2 x 512 MiB at
+    n = 512) are larger than L2."""
+    import numpy as np
+    import torch
+
+    from paper_1902_10345_gb300 import binding, build, inputs
+
+    build.build()
+    binding.lib()
+    n, T = a.size3d, a.T3d
+    g = inputs.uniform_box(n, n, n, seed=0)
+    x = torch.from_numpy(g).float().cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    updates = (n - 2) ** 3 * T
+    for _ in range(max(3, a.warmup)):
+        binding.jacobi3d(x, y, T)
+    torch.cuda.synchronize()
+    binding.check(binding.sdfg_device_error(True))
+    binding.sdfg_stats_reset()
+    binding.sdfg_stats_enable(True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for i in range(a.steps):
+            binding.jacobi3d(x, y, T)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+    binding.sdfg_stats_enable(False)
+    ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
+    med_ms, ci_ms = median_ci95(step_ms)
+    n_k, ms_k = binding.sdfg_stats_get("stencil3d")
+    n_c, _ = binding.sdfg_stats_get("copy")
+    binding.sdfg_stats_reset()
+    binding.check(binding.sdfg_device_error(True))
+    value = updates * a.steps / (ms / 1e3) / 1e9
+    # end to end through the public API with host buffers: pinned host ->
+    # device, T steps, device -> pinned host, every step
+    hx = x.cpu().pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    dx = torch.empty_like(x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        dx.copy_(hx, non_blocking=True)
+        binding.jacobi3d(dx, y, T)
+        hy.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    assert torch.equal(hy.cuda(), y), "end-to-end result differs from the device-resident result"
+    hbm, hbm_src = measured_peaks()
+    bytes_per_launch = (n - 2) ** 3 * 2 * 4        # one read and one write per interior point and step
+    achieved = bytes_per_launch / (ms_k / n_k / 1e3) / 1e9 if n_k else None
+    cpu = None
+    if not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        gd = x.double().cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.jacobi3d(gd, 1, threads=0)
+        dt1 = time.perf_counter() - t0
+        T_s = int(max(1, min(T, a.cpu_seconds / max(dt1, 1e-3))))
+        t0 = time.perf_counter()
+        oracle.jacobi3d(gd, T_s, threads=0)
+        el = time.perf_counter() - t0
+        cpu = {"value": (n - 2) ** 3 * T_s / el / 1e9, "unit": UNIT, "cores": oracle.num_threads(0), "kind": "oracle",
+               "sample": f"{n}^3 box, FP64 3-D oracle, {T_s} of {T} timesteps, all host threads, {el:.1f} s",
+               "cpu_model": cpu_model()}
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": max(3, a.warmup),
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "step_ms": {"median": med_ms, "ci95": ci_ms, "min": min(step_ms), "max": max(step_ms)},
+        "config": {"workload": f"jacobi3d_{n}cube_f32_T{T}", "depth": n, "rows": n, "cols": n, "T": T,
+                   "kernel": "stencil3d (one launch per step)", "tile": "16 rows x 120 cols, planes streamed",
+                   "l2": f"inputs larger than L2 (two {n ** 3 * 4 >> 20} MiB boxes), no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src,
+                     "kernel": "jacobi3d_kernel", "k": 1, "launches_per_step": n_k / a.steps if n_k else 0,
+                     "avg_launch_ms": (ms_k / n_k) if n_k else None, "roofline_gupdates": hbm / 8,
+                     "kernel_share_of_step": (ms_k / ms) if ms else None},
+        "cpu_baseline": cpu,
+        "e2e": {"value": updates * a.steps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": n ** 3 * 4,
+                "d2h_bytes_per_step": n ** 3 * 4},
+        "clocks": clk.summary(),
+        "gpu_launches": n_k + n_c,
+    }))
+
+
 # ------------------------------------------------------------------- serve -------
 def _pct(v, q):
     import numpy as np
@@ -724,6 +822,8 @@ def main():
         run_precision(a)
     elif a.workload == "serve":
         run_serve(a)
+    elif a.workload == "3d":
+        run_3d(a)
     elif a.workload == "paper":
         run_paper(a)
     else:

@@ -238,6 +238,27 @@ int sdfg_server_destroy(sdfg_server *server);
  */
 int sdfg_laplace1d(double *A, int N, int T, void *stream);
 
+/*
+ * The Jacobi method one dimension up (paper Sec. 6.1's stencil benchmark and
+ * Fig. 1's ping-pong state loop, in 3-D): a 7-point stencil on a device box of
+ * depth x rows x cols elements of type dtype (sdfg_dtype), row pitch ld
+ * elements (ld >= cols), plane pitch rows * ld, planes contiguous.  For T
+ * timesteps every interior point becomes
+ *   (1/7) * (c + (((n + s) + (w + e)) + (u + d)))
+ * (n, s: rows i-1, i+1; w, e: columns j-1, j+1; u, d: planes z-1, z+1), in
+ * that order, round to nearest, in FP32 (FP32 and BF16 storage; BF16 is
+ * rounded when each step is stored) or FP64 (bit-identical to a plain FP64
+ * loop).  The one-cell outer shell keeps its input values.  out receives the
+ * whole box after T steps; in is read only; in == out is allowed; T = 0, or
+ * an extent below 3, copies.  in/out should be 16-byte aligned with ld *
+ * sizeof(element) a multiple of 16; otherwise the box is staged through an
+ * aligned copy.  Scratch: one box (two when staged), stream-ordered.
+ * Asynchronous on `stream`.  SDFG_ERR_INVAL for negative extents or T, ld <
+ * cols, an unknown dtype or a null pointer with a non-empty box.
+ */
+int sdfg_jacobi3d(const void *in, void *out, int depth, int rows, int cols, int ld, int T, int dtype,
+                  void *stream);
+
 /* Autotuner: times candidate configurations for this shape and dtype on the
  * calling stream, caches the best by shape class, and returns it. */
 int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *best, void *stream);
@@ -254,7 +275,8 @@ int sdfg_autotune_batch(const sdfg_desc *desc, int n, int check_stride, sdfg_con
 int sdfg_stats_enable(int on);
 int sdfg_stats_reset(void);
 /* Sums over launches of kernel family `name` ("naive", "temporal",
- * "persistent", "reduce", "copy"); waits for the recorded events. */
+ * "persistent", "reduce", "copy", "stencil3d"); waits for the recorded
+ * events. */
 int sdfg_stats_get(const char *name, long long *launches, double *total_ms);
 
 /* Reads (and with clear != 0 resets) the current device's error word. */

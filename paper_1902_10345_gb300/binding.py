@@ -67,6 +67,7 @@ _PROTOS = {
     "sdfg_server_snapshot": (_I, [_VP, ctypes.c_uint64]),
     "sdfg_server_destroy": (_I, [_VP]),
     "sdfg_laplace1d": (_I, [_VP, _I, _I, _VP]),
+    "sdfg_jacobi3d": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _I, _VP]),
     "sdfg_autotune": (_I, [_I, _I, _I, _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_autotune_batch": (_I, [ctypes.POINTER(sdfg_desc), _I, _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_stats_enable": (_I, [_I]),
@@ -158,6 +159,10 @@ def sdfg_laplace1d(A: int, N: int, T: int, stream: int = 0) -> int:
     return lib().sdfg_laplace1d(A, N, T, stream)
 
 
+def sdfg_jacobi3d(inp: int, out: int, D: int, R: int, C: int, ld: int, T: int, dtype: int, stream: int = 0) -> int:
+    return lib().sdfg_jacobi3d(inp, out, D, R, C, ld, T, dtype, stream)
+
+
 def sdfg_autotune(rows, cols, T, dtype, stream=0) -> sdfg_config:
     c = sdfg_config()
     check(lib().sdfg_autotune(rows, cols, T, dtype, ctypes.byref(c), stream))
@@ -235,6 +240,23 @@ def jacobi2d(inp, out, T: int, cfg: sdfg_config | None = None, stream=None) -> N
     if (R, C, ld) != (R2, C2, ld2) or inp.dtype != out.dtype:
         raise ValueError("in and out must have the same shape, pitch and dtype")
     check(sdfg_jacobi2d_cfg(pi, po, R, C, ld, T, dtype_code(inp), cfg, _stream(stream)))
+
+
+def _box_args(t):
+    """(pointer, depth, rows, cols, ld) of a 3-D tensor whose planes are rows * ld apart."""
+    if t.dim() != 3 or t.stride(2) != 1 or t.stride(0) != t.shape[1] * t.stride(1):
+        raise ValueError("box must be a 3-D tensor with unit column stride and planes rows * ld apart")
+    return t.data_ptr(), t.shape[0], t.shape[1], t.shape[2], t.stride(1)
+
+
+def jacobi3d(inp, out, T: int, stream=None) -> None:
+    """out <- inp after T timesteps of the 7-point stencil (device tensors of
+    equal shape, pitch and dtype; may be the same)."""
+    pi, D, R, C, ld = _box_args(inp)
+    po, D2, R2, C2, ld2 = _box_args(out)
+    if (D, R, C, ld) != (D2, R2, C2, ld2) or inp.dtype != out.dtype:
+        raise ValueError("in and out must have the same shape, pitch and dtype")
+    check(sdfg_jacobi3d(pi, po, D, R, C, ld, T, dtype_code(inp), _stream(stream)))
 
 
 def desc_for(inp, out, T: int, tol: float = 0.0, t_start: int = 0, r_first2: float = 0.0,

@@ -104,6 +104,28 @@ int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols
     return SDFG_OK;
 }
 
+int encode_tmap3d(CUtensorMap *tm, const void *base, int dtype, int depth, int rows, int cols, int ld, int box_cols,
+                  int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return set_error(SDFG_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const CUtensorMapDataType t = dtype == SDFG_F64    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                  : dtype == SDFG_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t S = static_cast<cuuint64_t>(dtype_bytes(dtype));
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows),
+                                static_cast<cuuint64_t>(depth)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * S, static_cast<cuuint64_t>(ld) * rows * S};
+    const cuuint32_t box[3] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(tm, t, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return set_error(SDFG_ERR_CUDA, "cuTensorMapEncodeTiled (3-D) failed (%d) for %dx%dx%d ld=%d",
+                         static_cast<int>(r), depth, rows, cols, ld);
+    return SDFG_OK;
+}
+
 // --------------------------------------------------------------- scratch ------
 int scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
@@ -180,7 +202,7 @@ struct Rec {
 std::mutex g_stats_mu;
 bool g_stats_on = false;
 std::vector<Rec> g_recs;
-const char *kFamilies[FAM_COUNT] = {"naive", "temporal", "persistent", "reduce", "copy"};
+const char *kFamilies[FAM_COUNT] = {"naive", "temporal", "persistent", "reduce", "copy", "stencil3d"};
 }  // namespace
 
 static thread_local bool g_stats_suspended = false;

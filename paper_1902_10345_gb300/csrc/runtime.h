@@ -47,6 +47,10 @@ inline int dtype_bytes(int dt) { return dt == SDFG_F64 ? 8 : (dt == SDFG_BF16 ? 
 // 2-D tensor map over a rows x cols grid with pitch ld; box = box_cols x CHUNK_ROWS;
 // out-of-range elements read as zero.
 int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols, int ld, int box_cols);
+// Rank-3 map over a depth x rows x cols box (row pitch ld elements, plane
+// pitch rows*ld): boxes of box_cols x box_rows x 1.
+int encode_tmap3d(CUtensorMap *tm, const void *base, int dtype, int depth, int rows, int cols, int ld, int box_cols,
+                  int box_rows);
 // True when a buffer can be read by TMA as laid out.
 inline bool tma_compatible(const void *p, int ld, int dtype) {
     return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((static_cast<long long>(ld) * dtype_bytes(dtype)) % 16 == 0);
@@ -72,7 +76,7 @@ struct TimedLaunch {
     int family = -1;
     bool active() const { return family >= 0; }
 };
-enum Family { FAM_NAIVE = 0, FAM_TEMPORAL, FAM_PERSISTENT, FAM_REDUCE, FAM_COPY, FAM_COUNT };
+enum Family { FAM_NAIVE = 0, FAM_TEMPORAL, FAM_PERSISTENT, FAM_REDUCE, FAM_COPY, FAM_STENCIL3D, FAM_COUNT };
 TimedLaunch stats_begin(int family, cudaStream_t s);
 // No launch is timed on this thread while suspended (stream capture).
 void stats_suspend(bool on);

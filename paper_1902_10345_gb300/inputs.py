@@ -37,6 +37,12 @@ def uniform_grid(rows: int, cols: int, seed: int = 0) -> np.ndarray:
     return rng_for(seed).random((rows, cols))
 
 
+def uniform_box(depth: int, rows: int, cols: int, seed: int = 0) -> np.ndarray:
+    """depth x rows x cols draw of uniform[0,1) in one row-major call (shell
+    included): the 3-D counterpart of uniform_grid."""
+    return rng_for(seed).random((depth, rows, cols))
+
+
 # --- the five workload recipes -------------------------------------------------
 
 SINGLE_SMALL = dict(rows=256, cols=256, T=100, seed=0)        # FP64 parity case
