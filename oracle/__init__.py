@@ -4,10 +4,13 @@ and the 1-D Laplace program of the paper's Fig. 1.
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 ``bench.py``'s CPU-baseline leg (and its ``--impl reference`` arm) may import
 this package.  The CUDA library never calls it, and the two share no code:
-this wrapper loads ``jacobi2d_oracle.c`` and ``jacobi3d_oracle.c``, each
+this wrapper loads ``jacobi2d_oracle.c``, ``jacobi3d_oracle.c`` and
+``sor2d_oracle.c``, each
 compiled by gcc with ``-O2 -ffp-contract=off`` (no fast-math), nothing else.
 
 ``laplace1d`` is the 1-D Laplace program printed in the paper's Fig. 1.
+``sor2d`` is the in-place, ordered counterpart: red-black successive
+over-relaxation of the same 2-D Laplace problem (``sor2d_oracle.c``).
 ``jacobi3d`` is the same method as the 2-D Jacobi stencil one dimension up
 (7 points, weight 1/7 each, fixed one-cell shell); the C file's header gives
 the formula and its readings.
@@ -30,8 +33,10 @@ thread-count invariance, closed-form stopping step), ``laplace1d`` by
 ``tests/test_oracle_laplace1d.py`` and ``jacobi3d`` by
 ``tests/test_oracle_jacobi3d.py`` (hand-computed 4x4x4 fixtures, closed-form
 eigenmodes, harmonic fixed points, maximum principle, symmetries, semigroup,
-thread-count invariance); mutation tests plant mistakes in a copy of each C
-source and check that the pins catch them.
+thread-count invariance) and ``sor2d`` by ``tests/test_oracle_sor2d.py``
+(hand-computed sweeps, Young's convergence rates for red-black ordering,
+harmonic fixed points, exact rationals, symmetry); mutation tests plant
+mistakes in a copy of each C source and check that the pins catch them.
 """
 from __future__ import annotations
 
@@ -45,12 +50,15 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "jacobi2d_oracle.c")
 _SRC3D = os.path.join(_HERE, "jacobi3d_oracle.c")
+_SRCSOR = os.path.join(_HERE, "sor2d_oracle.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
 _LIB3D_PATH = os.path.join(_BUILD_DIR, "liboracle3d.so")
+_LIBSOR_PATH = os.path.join(_BUILD_DIR, "liboraclesor.so")
 _lock = threading.Lock()
 _lib = None
 _lib3d = None
+_libsor = None
 
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c99"]
 
@@ -65,10 +73,10 @@ def compile_source(src: str, out: str) -> str:
 
 
 def build(force: bool = False) -> str:
-    """Build liboracle.so and liboracle3d.so (each only if missing or older
-    than its source); returns the 2-D library's path."""
+    """Build liboracle.so, liboracle3d.so and liboraclesor.so (each only if
+    missing or older than its source); returns the 2-D library's path."""
     with _lock:
-        for src, lib in ((_SRC, _LIB_PATH), (_SRC3D, _LIB3D_PATH)):
+        for src, lib in ((_SRC, _LIB_PATH), (_SRC3D, _LIB3D_PATH), (_SRCSOR, _LIBSOR_PATH)):
             if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
                 compile_source(src, lib)
     return _LIB_PATH
@@ -104,6 +112,22 @@ def _get():
     if _lib is None:
         _lib = load_library(build())
     return _lib
+
+
+def load_library_sor(path: str) -> ctypes.CDLL:
+    lib = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_sor2d.argtypes = [dp, dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double]
+    lib.oracle_sor2d.restype = ctypes.c_int
+    return lib
+
+
+def _getsor():
+    global _libsor
+    if _libsor is None:
+        build()
+        _libsor = load_library_sor(_LIBSOR_PATH)
+    return _libsor
 
 
 def _get3d():
@@ -214,3 +238,16 @@ def jacobi3d_window(box, T: int, lo, hi, threads: int = 1, lib=None) -> np.ndarr
             raise ValueError("window out of range")
     crop = jacobi3d(a[cl[0]:ch[0], cl[1]:ch[1], cl[2]:ch[2]], T, threads=threads, lib=lib)
     return crop[lo[0] - cl[0]:hi[0] - cl[0], lo[1] - cl[1]:hi[1] - cl[1], lo[2] - cl[2]:hi[2] - cl[2]]
+
+
+def sor2d(grid, T: int, omega: float, lib=None) -> np.ndarray:
+    """Grid after T red-black SOR iterations with relaxation omega (FP64; the
+    input is converted to FP64 exactly): red points (i + j even) first, then
+    black, each updated in place from its four neighbours."""
+    lib = lib or _getsor()
+    a = _as_f64(grid)
+    out = np.empty_like(a)
+    rc = lib.oracle_sor2d(_dptr(a), _dptr(out), a.shape[0], a.shape[1], int(T), float(omega))
+    if rc != 0:
+        raise ValueError(f"oracle_sor2d failed with status {rc}")
+    return out

@@ -123,3 +123,39 @@ def test_jacobi3d_mutant_is_caught(name, tmp_path):
         except AssertionError:
             caught.append(pin.__name__)
     assert caught, f"no pin caught mutant {name}"
+
+
+# ---- the red-black SOR oracle (oracle_sor2d) -------------------------------------------
+from tests import test_oracle_sor2d as _sor  # noqa: E402
+
+SRCSOR = os.path.join(os.path.dirname(oracle.__file__), "sor2d_oracle.c")
+
+SOR_MUTANTS = {
+    "black_first": ("        sor_colour(out, R, C, 0, a, b);\n        sor_colour(out, R, C, 1, a, b);",
+                    "        sor_colour(out, R, C, 1, a, b);\n        sor_colour(out, R, C, 0, a, b);"),
+    "colour_parity": ("j = 1 + ((i + 1 + colour) & 1);", "j = 1 + ((i + colour) & 1);"),
+    "lexicographic": ("for (; j < C - 1; j += 2) {", "for (j = 1; j < C - 1; j += 1) {"),
+    "weight": ("b = 0.25 * omega;", "b = 0.2 * omega;"),
+    "relaxation": ("a = 1.0 - omega;", "a = omega - 1.0;"),
+    "south_index": ("double q = (north[j] + south[j]) + (row[j - 1] + row[j + 1]);",
+                    "double q = (north[j] + south[j + 1]) + (row[j - 1] + row[j + 1]);"),
+    "last_row_skipped": ("for (i = 1; i < R - 1; ++i) {", "for (i = 1; i < R - 2; ++i) {"),
+    "off_by_one_T": ("for (t = 1; t <= T; ++t) {", "for (t = 2; t <= T; ++t) {"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SOR_MUTANTS))
+def test_sor_mutant_is_caught(name, tmp_path):
+    old, new = SOR_MUTANTS[name]
+    src = open(SRCSOR).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    path = tmp_path / f"mutsor_{name}.c"
+    path.write_text(src.replace(old, new, 1))
+    lib = oracle.load_library_sor(oracle.compile_source(str(path), str(tmp_path / f"libmutsor_{name}.so")))
+    caught = []
+    for pin in _sor.ALL_PINS:
+        try:
+            pin(lib)
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, f"no pin caught mutant {name}"
