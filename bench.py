@@ -50,10 +50,13 @@ def parse():
     p.add_argument("--kernel", choices=["persistent", "temporal"], default="persistent")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
-    p.add_argument("--workload", choices=["single", "batch", "precision", "serve", "paper", "3d"], default="single",
+    p.add_argument("--workload", choices=["single", "batch", "precision", "serve", "paper", "3d", "sor"],
+                   default="single",
                    help="single: 8192^2 FP32 T=1000 (the default line); batch: 512 uneven grids in one "
                         "persistent launch; precision: 4 x 16384^2 T=500 FP32 and BF16; serve: Laplace requests; "
-                        "3d: the 7-point stencil on a 512^3 FP32 box, T=100")
+                        "3d: the 7-point stencil on a 512^3 FP32 box, T=100; sor: red-black SOR on the 8192^2 "
+                        "FP32 grid, omega 1.9, 1000 iterations")
+    p.add_argument("--omega", type=float, default=1.9, help="sor: relaxation factor")
     p.add_argument("--size3d", type=int, default=512, help="3d: box edge")
     p.add_argument("--T3d", type=int, default=100, help="3d: timesteps")
     p.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
@@ -330,7 +333,7 @@ def run_ours(a):
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
     med_ms, ci_ms = median_ci95(step_ms)
     launches = {}
-    for fam in ("naive", "temporal", "persistent", "reduce", "copy", "stencil3d"):
+    for fam in ("naive", "temporal", "persistent", "reduce", "copy", "stencil3d", "sor"):
         launches[fam] = binding.sdfg_stats_get(fam)
     binding.sdfg_stats_reset()
     binding.check(binding.sdfg_device_error(True))
@@ -689,6 +692,102 @@ def run_3d(a):
     }))
 
 
+# ---------------------------------------------------------------------- SOR -------
+def run_sor(a):
+    """Red-black SOR on the default grid (8192^2 FP32, uniform [0,1) from
+    seed 0, boundary ring fixed), a.T iterations of relaxation a.omega, one
+    launch per iteration; inputs (2 x 256 MiB) are larger than L2."""
+    import torch
+
+    from paper_1902_10345_gb300 import binding, build, inputs
+
+    build.build()
+    binding.lib()
+    R, C, T, om = a.rows, a.cols, a.T, a.omega
+    x = torch.from_numpy(inputs.uniform_grid(R, C, seed=0)).float().cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    updates = (R - 2) * (C - 2) * T
+    for _ in range(max(3, a.warmup)):
+        binding.sor2d(x, y, T, om)
+    torch.cuda.synchronize()
+    binding.check(binding.sdfg_device_error(True))
+    binding.sdfg_stats_reset()
+    binding.sdfg_stats_enable(True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for i in range(a.steps):
+            binding.sor2d(x, y, T, om)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+    binding.sdfg_stats_enable(False)
+    ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
+    med_ms, ci_ms = median_ci95(step_ms)
+    n_k, ms_k = binding.sdfg_stats_get("sor")
+    n_c, _ = binding.sdfg_stats_get("copy")
+    binding.sdfg_stats_reset()
+    binding.check(binding.sdfg_device_error(True))
+    value = updates * a.steps / (ms / 1e3) / 1e9
+    hx = x.cpu().pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    dx = torch.empty_like(x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        dx.copy_(hx, non_blocking=True)
+        binding.sor2d(dx, y, T, om)
+        hy.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    assert torch.equal(hy.cuda(), y), "end-to-end result differs from the device-resident result"
+    hbm, hbm_src = measured_peaks()
+    bytes_per_launch = (R - 2) * (C - 2) * 2 * 4     # one read and one write per interior point and iteration
+    achieved = bytes_per_launch / (ms_k / n_k / 1e3) / 1e9 if n_k else None
+    wl = f"sor2d_{R}x{C}_f32_T{T}_omega{om:g}"
+    traffic = committed_traffic(build.kernel_digest(build.KERNEL_FILES_SOR), wl)
+    cpu = None
+    if not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        gd = x.double().cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.sor2d(gd, 1, om)
+        t1 = time.perf_counter()
+        oracle.sor2d(gd, 3, om)
+        t2 = time.perf_counter()
+        dt1 = max((t2 - t1) - (t1 - t0), 1e-3) / 2
+        T_s = int(max(1, min(T, a.cpu_seconds / dt1)))
+        t0 = time.perf_counter()
+        oracle.sor2d(gd, T_s, om)
+        el = time.perf_counter() - t0
+        cpu = {"value": (R - 2) * (C - 2) * T_s / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{R}x{C} grid, FP64 red-black SOR oracle (one thread), {T_s} of {T} iterations, {el:.1f} s",
+               "cpu_model": cpu_model()}
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": max(3, a.warmup),
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "step_ms": {"median": med_ms, "ci95": ci_ms, "min": min(step_ms), "max": max(step_ms)},
+        "config": {"workload": wl, "rows": R, "cols": C, "T": T, "omega": om,
+                   "kernel": "sor2d (one launch per red-black iteration)", "tile": "60 rows x 120 cols",
+                   "l2": "inputs larger than L2 (two 256 MiB grids), no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                     "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src,
+                     "kernel": "sor2d_kernel", "launches_per_step": n_k / a.steps if n_k else 0,
+                     "avg_launch_ms": (ms_k / n_k) if n_k else None, "roofline_gupdates": hbm / 8,
+                     "kernel_share_of_step": (ms_k / ms) if ms else None},
+        "cpu_baseline": cpu,
+        "e2e": {"value": updates * a.steps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": R * C * 4,
+                "d2h_bytes_per_step": R * C * 4},
+        "clocks": clk.summary(),
+        "gpu_launches": n_k + n_c,
+    }))
+
+
 # ------------------------------------------------------------------- serve -------
 def _pct(v, q):
     import numpy as np
@@ -830,6 +929,8 @@ def main():
         run_serve(a)
     elif a.workload == "3d":
         run_3d(a)
+    elif a.workload == "sor":
+        run_sor(a)
     elif a.workload == "paper":
         run_paper(a)
     else:

@@ -259,6 +259,28 @@ int sdfg_laplace1d(double *A, int N, int T, void *stream);
 int sdfg_jacobi3d(const void *in, void *out, int depth, int rows, int cols, int ld, int T, int dtype,
                   void *stream);
 
+/*
+ * Red-black successive over-relaxation of the same 2-D Laplace problem: the
+ * in-place, ordered counterpart of the Jacobi stencil (paper Sec. 6.1's
+ * stencil; each half-sweep is one Map of independent points).  One of T
+ * iterations updates every interior point with i + j even, then every one
+ * with i + j odd, each as
+ *   c <- (1 - omega) * c + (omega / 4) * ((n + s) + (w + e))
+ * in that order, round to nearest: FP32 arithmetic for FP32 and BF16
+ * storage (BF16 is rounded after each half-sweep), FP64 for FP64
+ * (bit-identical to a plain FP64 loop).  The coefficients (1 - omega) and
+ * omega / 4 are evaluated once in double.  omega = 1 is Gauss-Seidel; the
+ * iteration converges for 0 < omega < 2.  Grid: rows x cols, row pitch ld
+ * elements, device memory.  out receives the whole grid after T iterations;
+ * in is read only; in == out is allowed; T = 0, or an extent below 3,
+ * copies.  The boundary ring keeps its input values.  Alignment and scratch
+ * as for sdfg_jacobi3d.  Asynchronous on `stream`.  SDFG_ERR_INVAL for
+ * negative extents or T, ld < cols, a non-finite omega, an unknown dtype or
+ * a null pointer with a non-empty grid.
+ */
+int sdfg_sor2d(const void *in, void *out, int rows, int cols, int ld, int T, double omega, int dtype,
+               void *stream);
+
 /* Autotuner: times candidate configurations for this shape and dtype on the
  * calling stream, caches the best by shape class, and returns it. */
 int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *best, void *stream);
@@ -275,8 +297,8 @@ int sdfg_autotune_batch(const sdfg_desc *desc, int n, int check_stride, sdfg_con
 int sdfg_stats_enable(int on);
 int sdfg_stats_reset(void);
 /* Sums over launches of kernel family `name` ("naive", "temporal",
- * "persistent", "reduce", "copy", "stencil3d"); waits for the recorded
- * events. */
+ * "persistent", "reduce", "copy", "stencil3d", "sor"); waits for the
+ * recorded events. */
 int sdfg_stats_get(const char *name, long long *launches, double *total_ms);
 
 /* Reads (and with clear != 0 resets) the current device's error word. */

@@ -68,6 +68,7 @@ _PROTOS = {
     "sdfg_server_destroy": (_I, [_VP]),
     "sdfg_laplace1d": (_I, [_VP, _I, _I, _VP]),
     "sdfg_jacobi3d": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _I, _VP]),
+    "sdfg_sor2d": (_I, [_VP, _VP, _I, _I, _I, _I, ctypes.c_double, _I, _VP]),
     "sdfg_autotune": (_I, [_I, _I, _I, _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_autotune_batch": (_I, [ctypes.POINTER(sdfg_desc), _I, _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_stats_enable": (_I, [_I]),
@@ -257,6 +258,16 @@ def jacobi3d(inp, out, T: int, stream=None) -> None:
     if (D, R, C, ld) != (D2, R2, C2, ld2) or inp.dtype != out.dtype:
         raise ValueError("in and out must have the same shape, pitch and dtype")
     check(sdfg_jacobi3d(pi, po, D, R, C, ld, T, dtype_code(inp), _stream(stream)))
+
+
+def sor2d(inp, out, T: int, omega: float, stream=None) -> None:
+    """out <- inp after T red-black SOR iterations with relaxation omega
+    (device tensors of equal shape, pitch and dtype; may be the same)."""
+    pi, R, C, ld = _grid_args(inp)
+    po, R2, C2, ld2 = _grid_args(out)
+    if (R, C, ld) != (R2, C2, ld2) or inp.dtype != out.dtype:
+        raise ValueError("in and out must have the same shape, pitch and dtype")
+    check(lib().sdfg_sor2d(pi, po, R, C, ld, T, float(omega), dtype_code(inp), _stream(stream)))
 
 
 def desc_for(inp, out, T: int, tol: float = 0.0, t_start: int = 0, r_first2: float = 0.0,

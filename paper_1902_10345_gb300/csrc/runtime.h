@@ -76,7 +76,7 @@ struct TimedLaunch {
     int family = -1;
     bool active() const { return family >= 0; }
 };
-enum Family { FAM_NAIVE = 0, FAM_TEMPORAL, FAM_PERSISTENT, FAM_REDUCE, FAM_COPY, FAM_STENCIL3D, FAM_COUNT };
+enum Family { FAM_NAIVE = 0, FAM_TEMPORAL, FAM_PERSISTENT, FAM_REDUCE, FAM_COPY, FAM_STENCIL3D, FAM_SOR, FAM_COUNT };
 TimedLaunch stats_begin(int family, cudaStream_t s);
 // No launch is timed on this thread while suspended (stream capture).
 void stats_suspend(bool on);

@@ -1,0 +1,277 @@
+// Red-black successive over-relaxation of the 2-D 5-point Laplace problem:
+// the in-place, ordered counterpart of the Jacobi stencil (paper Sec. 6.1's
+// stencil on a 2-D domain with constant boundary).  One iteration updates
+// every interior point with i + j even ("red"), then every one with i + j odd
+// ("black"), each as
+//   c <- (1 - omega) * c + (omega / 4) * ((n + s) + (w + e))
+// in that order, round to nearest, no contraction, in FP32 (FP32 and BF16
+// storage) or FP64 (bit-identical to a plain FP64 loop).  A point of one
+// colour reads only points of the other colour, so each half-sweep is one
+// map of independent instances (the paper's Map scope).
+//
+// One launch is one iteration.  A CTA owns a tile of TY rows x TX columns and
+// loads it by 2-D TMA with a two-row and a 16-byte column halo into shared
+// memory.  It updates the red points of the tile plus a one-cell ring in
+// place (they read only black values, none of which change), synchronises,
+// updates the black points of the tile (reading the new red values, the ring
+// included), and writes the tile to the other buffer of a ping-pong pair, so
+// that no CTA reads a value another CTA has already advanced.  The result
+// equals the in-place sweep.  Boundary-ring points are copied; every point of
+// the grid is written by exactly one CTA.
+#include <algorithm>
+#include <math.h>
+
+#include "device_common.cuh"
+#include "runtime.h"
+
+namespace sdfg {
+
+#ifndef SDFG_SOR_TY
+#define SDFG_SOR_TY 60
+#endif
+constexpr int SOR_TY = SDFG_SOR_TY;     // output rows per tile (SOR_TY + 4 <= 256: one TMA box)
+constexpr int SOR_BY = SOR_TY + 4;      // rows per TMA box (two-row halo each side)
+constexpr int SOR_THREADS = 256;        // 8 warps
+
+struct SorGeo {
+    int R, C, ld;
+    int tiles_x;
+};
+
+__device__ __forceinline__ float sor_point(float c, float n, float s, float w, float e, float a, float b) {
+    return __fadd_rn(__fmul_rn(a, c), __fmul_rn(b, __fadd_rn(__fadd_rn(n, s), __fadd_rn(w, e))));
+}
+__device__ __forceinline__ double sor_point(double c, double n, double s, double w, double e, double a, double b) {
+    return __dadd_rn(__dmul_rn(a, c), __dmul_rn(b, __dadd_rn(__dadd_rn(n, s), __dadd_rn(w, e))));
+}
+
+template <class ST, int V>
+__global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constant__ CUtensorMap tm,
+                                                            ST *__restrict__ dst, const SorGeo g,
+                                                            typename Store<ST>::CT a, typename Store<ST>::CT b,
+                                                            int *err, unsigned long long timeout_ns) {
+    using CT = typename Store<ST>::CT;
+    constexpr int W = 32 * V;                 // box columns
+    constexpr int XH = Store<ST>::xalign;     // column halo (16 bytes, >= 2)
+    constexpr int TX = W - 2 * XH;            // output columns per tile
+    constexpr uint32_t BOX_BYTES = SOR_BY * W * sizeof(ST);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    ST *box = reinterpret_cast<ST *>(smem_raw);
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int tx = blockIdx.x % g.tiles_x;
+    const int ty = blockIdx.x / g.tiles_x;
+    const int x0 = tx * TX;                   // first output column
+    const int y0 = ty * SOR_TY;               // first output row
+    // box row r <-> grid row y0 - 2 + r; box column k <-> grid column x0 - XH + k
+    const int gx = x0 - XH + lane * V;        // grid column of this lane's element 0
+
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        tmap_prefetch(&tm);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar, BOX_BYTES);
+        tma_load_3d(box, &tm, x0 - XH, y0 - 2, 0, &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0, timeout_ns);
+    if (!__syncthreads_and(ok)) {
+        // give the copy a bounded chance to land before leaving, then report
+        mbar_wait_bounded(&bar, 0, 1000000ull);
+        if (tid == 0) set_device_error(err, DEV_ERR_TIMEOUT_TMA);
+        return;
+    }
+
+    // interior columns among this lane's V (fixed for the CTA)
+    unsigned colin = 0;
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+        if (gx + e >= 1 && gx + e <= g.C - 2) colin |= 1u << e;
+    // One half-sweep over box rows [r_lo, r_hi) for the interior points of
+    // colour `colour`, in place.  Every lane computes all V points and keeps
+    // the other colour's values, then writes its V values back as one vector:
+    // points of the other colour are rewritten with the value they already
+    // hold, and a point of this colour is read by no one in this half-sweep
+    // (its neighbours have the other colour).
+    auto half_sweep = [&](int colour, int r_lo, int r_hi) {
+        for (int r = r_lo + warp; r < r_hi; r += SOR_THREADS / 32) {
+            const int y = y0 - 2 + r;
+            if (y < 1 || y > g.R - 2) continue;   // warp-uniform
+            ST *row = box + r * W + lane * V;
+            CT c[V], n[V], s[V];
+            VecIO<ST, V>::load(c, row);
+            VecIO<ST, V>::load(n, row - W);
+            VecIO<ST, V>::load(s, row + W);
+            // west of element 0 and east of element V-1 from the neighbouring
+            // lanes (lanes 0 and 31 get stale values: their columns are halo,
+            // beyond the one-cell ring the red sweep needs)
+            const CT left = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
+            const CT right = __shfl_down_sync(FULL_MASK, c[0], 1);
+            // element e has colour (y + gx + e) & 1
+            const unsigned pick = colin & ((((y + gx + colour) & 1) == 0) ? 0x55555555u : 0xaaaaaaaau);
+            CT o[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const CT w = e == 0 ? left : c[e - 1];
+                const CT ea = e == V - 1 ? right : c[e + 1];
+                const CT v = sor_point(c[e], n[e], s[e], w, ea, a, b);
+                o[e] = ((pick >> e) & 1u) ? v : c[e];
+            }
+            VecIO<ST, V>::store(row, o);
+        }
+    };
+    // red on the tile and a one-cell ring (box rows 1 .. BY-2), then black on
+    // the tile (box rows 2 .. BY-3)
+    half_sweep(0, 1, SOR_BY - 1);
+    __syncthreads();
+    half_sweep(1, 2, SOR_BY - 2);
+    __syncthreads();
+
+    // write the tile
+    const bool own_cols = lane * V >= XH && lane * V < XH + TX && gx < g.C;
+    if (own_cols) {
+        const bool full_vec = gx + V <= g.C;
+        for (int r = 2 + warp; r < SOR_BY - 2; r += SOR_THREADS / 32) {
+            const int y = y0 - 2 + r;
+            if (y >= g.R) break;
+            const ST *row = box + r * W + lane * V;
+            ST *q = dst + static_cast<long long>(y) * g.ld + gx;
+            if (full_vec) {
+                CT v[V];
+                VecIO<ST, V>::load(v, row);
+                VecIO<ST, V>::store(q, v);
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    if (gx + e < g.C) q[e] = row[e];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host -----
+static const void *sor_kernel(int dtype) {
+    switch (dtype) {
+        case SDFG_F32: return reinterpret_cast<const void *>(&sor2d_kernel<float, 4>);
+        case SDFG_BF16: return reinterpret_cast<const void *>(&sor2d_kernel<__nv_bfloat16, 4>);
+        default: return reinterpret_cast<const void *>(&sor2d_kernel<double, 2>);
+    }
+}
+
+static int sor_box_cols(int dtype) { return dtype == SDFG_F64 ? 64 : 128; }
+static int sor_tile_cols(int dtype) { return sor_box_cols(dtype) - 2 * (16 / dtype_bytes(dtype)); }
+
+static int launch_sor(const CUtensorMap &tm, void *dst, const SorGeo &g, int dtype, double omega, int *err,
+                      cudaStream_t s) {
+    const void *fn = sor_kernel(dtype);
+    const size_t smem = static_cast<size_t>(SOR_BY) * sor_box_cols(dtype) * dtype_bytes(dtype);
+    CUtensorMap t = tm;
+    SorGeo gg = g;
+    void *dp = dst;
+    unsigned long long to = DEFAULT_TIMEOUT_NS;
+    // the two coefficients, evaluated once in double and then converted to
+    // the compute type
+    const double ad = 1.0 - omega, bd = 0.25 * omega;
+    float af = static_cast<float>(ad), bf = static_cast<float>(bd);
+    double a64 = ad, b64 = bd;
+    void *args_f[] = {&t, &dp, &gg, &af, &bf, &err, &to};
+    void *args_d[] = {&t, &dp, &gg, &a64, &b64, &err, &to};
+    const unsigned blocks = static_cast<unsigned>(static_cast<long long>(g.tiles_x) * ((g.R + SOR_TY - 1) / SOR_TY));
+    TimedLaunch tl = stats_begin(FAM_SOR, s);
+    cudaError_t e = cudaLaunchKernel(fn, dim3(blocks), dim3(SOR_THREADS), dtype == SDFG_F64 ? args_d : args_f, smem, s);
+    stats_end(tl, s);
+    if (e != cudaSuccess) return cuda_error(e, "sor2d launch");
+    return SDFG_OK;
+}
+
+static bool sor_tma_ok(const void *p, int ld, int dtype) {
+    return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((static_cast<long long>(ld) * dtype_bytes(dtype)) % 16 == 0);
+}
+
+}  // namespace sdfg
+
+using namespace sdfg;
+
+extern "C" int sdfg_sor2d(const void *in, void *out, int rows, int cols, int ld, int T, double omega, int dtype,
+                          void *stream) {
+    if (rows < 0 || cols < 0 || T < 0 || !dtype_valid(dtype) || !isfinite(omega))
+        return set_error(SDFG_ERR_INVAL, "sdfg_sor2d: bad extents, T, omega or dtype (%d x %d, T=%d, dtype %d)", rows,
+                         cols, T, dtype);
+    if (ld < cols) return set_error(SDFG_ERR_INVAL, "sdfg_sor2d: ld %d < cols %d", ld, cols);
+    if (rows == 0 || cols == 0) return SDFG_OK;
+    if (!in || !out) return set_error(SDFG_ERR_INVAL, "sdfg_sor2d: null grid");
+    DeviceState *st = nullptr;
+    int rc = current_device(&st);
+    if (rc != SDFG_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (T == 0 || rows < 3 || cols < 3) {
+        if (in == out) return SDFG_OK;
+        return launch_copy2d(out, ld, in, ld, rows, cols, dtype, s);
+    }
+    const size_t S = dtype_bytes(dtype);
+    const bool aligned = sor_tma_ok(in, ld, dtype) && sor_tma_ok(out, ld, dtype);
+    const int ldw = aligned ? ld : (cols + 31) / 32 * 32;
+    const size_t bytes = static_cast<size_t>(rows) * ldw * S;
+    void *a = nullptr, *b = nullptr;
+    const void *src0 = in;
+    void *first = nullptr, *second = nullptr;
+    if (aligned) {
+        rc = scratch_alloc(&a, bytes, s);
+        if (rc != SDFG_OK) return rc;
+        if (in != out) {
+            first = (T % 2 == 1) ? out : a;
+            second = first == out ? a : out;
+        } else {
+            first = a;
+            second = out;
+        }
+    } else {
+        rc = scratch_alloc(&a, bytes, s);
+        if (rc == SDFG_OK) rc = scratch_alloc(&b, bytes, s);
+        if (rc == SDFG_OK) rc = launch_copy2d(a, ldw, in, ld, rows, cols, dtype, s);
+        if (rc != SDFG_OK) {
+            scratch_free(a, s);
+            scratch_free(b, s);
+            return rc;
+        }
+        src0 = a;
+        first = b;
+        second = a;
+    }
+    const void *fn = sor_kernel(dtype);
+    const size_t smem = static_cast<size_t>(SOR_BY) * sor_box_cols(dtype) * S;
+    static bool attr_done[3] = {false, false, false};
+    if (!attr_done[dtype]) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) rc = cuda_error(e, "sor2d attribute");
+        else attr_done[dtype] = true;
+    }
+    const int box_cols = sor_box_cols(dtype);
+    alignas(128) CUtensorMap tm_src0, tm_first, tm_second;
+    if (rc == SDFG_OK) rc = encode_tmap3d(&tm_src0, src0, dtype, 1, rows, cols, ldw, box_cols, SOR_BY);
+    if (rc == SDFG_OK) rc = encode_tmap3d(&tm_first, first, dtype, 1, rows, cols, ldw, box_cols, SOR_BY);
+    if (rc == SDFG_OK) rc = encode_tmap3d(&tm_second, second, dtype, 1, rows, cols, ldw, box_cols, SOR_BY);
+    SorGeo g;
+    g.R = rows;
+    g.C = cols;
+    g.ld = ldw;
+    g.tiles_x = (cols + sor_tile_cols(dtype) - 1) / sor_tile_cols(dtype);
+    const CUtensorMap *tsrc = &tm_src0;
+    void *dst = first;
+    void *fin = const_cast<void *>(src0);
+    for (int t = 0; t < T && rc == SDFG_OK; ++t) {
+        rc = launch_sor(*tsrc, dst, g, dtype, omega, st->d_err, s);
+        fin = dst;
+        tsrc = dst == first ? &tm_first : &tm_second;
+        dst = dst == first ? second : first;
+    }
+    if (rc == SDFG_OK && fin != out) rc = launch_copy2d(out, ld, fin, ldw, rows, cols, dtype, s);
+    scratch_free(a, s);
+    scratch_free(b, s);
+    return rc;
+}
