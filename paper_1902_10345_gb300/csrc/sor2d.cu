@@ -9,15 +9,18 @@
 // colour reads only points of the other colour, so each half-sweep is one
 // map of independent instances (the paper's Map scope).
 //
-// One launch is one iteration.  A CTA owns a tile of TY rows x TX columns and
-// loads it by 2-D TMA with a two-row and a 16-byte column halo into shared
-// memory.  It updates the red points of the tile plus a one-cell ring in
-// place (they read only black values, none of which change), synchronises,
-// updates the black points of the tile (reading the new red values, the ring
-// included), and writes the tile to the other buffer of a ping-pong pair, so
-// that no CTA reads a value another CTA has already advanced.  The result
-// equals the in-place sweep.  Boundary-ring points are copied; every point of
-// the grid is written by exactly one CTA.
+// One launch runs up to KI iterations (2 KI half-sweeps; StateFusion, paper
+// App. B).  A CTA owns a tile of TY rows x TX columns and loads it by 2-D TMA
+// with a halo of 2 KI rows and at least 2 KI columns on each side into shared
+// memory.  Half-sweep h updates, in place, the points of its colour on box
+// rows [1 + h, BY - 1 - h): they read only points of the other colour, none
+// of which change during the half-sweep, and the region shrinks by one row
+// and one column per half-sweep, exactly as far as a half-sweep's values
+// spread.  A barrier separates the half-sweeps.  The tile is then written to
+// the other buffer of a ping-pong pair, so that no CTA reads a value another
+// CTA has already advanced.  The result equals the in-place sweeps.
+// Boundary-ring points are copied; every point of the grid is written by
+// exactly one CTA.
 #include <algorithm>
 #include <math.h>
 
@@ -29,9 +32,21 @@ namespace sdfg {
 #ifndef SDFG_SOR_TY
 #define SDFG_SOR_TY 60
 #endif
-constexpr int SOR_TY = SDFG_SOR_TY;     // output rows per tile (SOR_TY + 4 <= 256: one TMA box)
-constexpr int SOR_BY = SOR_TY + 4;      // rows per TMA box (two-row halo each side)
+constexpr int SOR_TY = SDFG_SOR_TY;     // output rows per tile
 constexpr int SOR_THREADS = 256;        // 8 warps
+
+// Iterations per launch: 4 for FP32 and BF16 storage (a 16-byte column halo
+// of 8 elements or more), 2 for FP64 (a 32-byte halo of 4 doubles).
+template <class ST> struct SorShape {
+    static constexpr int KI = sizeof(ST) == 8 ? 2 : 4;
+    static constexpr int HR = 2 * KI;                         // halo rows (and least halo columns)
+    static constexpr int V = sizeof(ST) == 8 ? 2 : 4;         // columns per lane
+    static constexpr int XA = Store<ST>::xalign;              // TMA x alignment (elements)
+    static constexpr int XH = (HR + XA - 1) / XA * XA;        // halo columns
+    static constexpr int W = 32 * V;                          // box columns
+    static constexpr int TX = W - 2 * XH;                     // output columns per tile
+    static constexpr int BY = SOR_TY + 2 * HR;                // box rows (<= 256: one TMA box)
+};
 
 struct SorGeo {
     int R, C, ld;
@@ -45,15 +60,19 @@ __device__ __forceinline__ double sor_point(double c, double n, double s, double
     return __dadd_rn(__dmul_rn(a, c), __dmul_rn(b, __dadd_rn(__dadd_rn(n, s), __dadd_rn(w, e))));
 }
 
-template <class ST, int V>
+template <class ST>
 __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constant__ CUtensorMap tm,
                                                             ST *__restrict__ dst, const SorGeo g,
                                                             typename Store<ST>::CT a, typename Store<ST>::CT b,
-                                                            int *err, unsigned long long timeout_ns) {
+                                                            int n_half, int *err, unsigned long long timeout_ns) {
     using CT = typename Store<ST>::CT;
-    constexpr int W = 32 * V;                 // box columns
-    constexpr int XH = Store<ST>::xalign;     // column halo (16 bytes, >= 2)
-    constexpr int TX = W - 2 * XH;            // output columns per tile
+    using SH = SorShape<ST>;
+    constexpr int V = SH::V;
+    constexpr int W = SH::W;
+    constexpr int XH = SH::XH;
+    constexpr int TX = SH::TX;
+    constexpr int HR = SH::HR;
+    constexpr int SOR_BY = SH::BY;
     constexpr uint32_t BOX_BYTES = SOR_BY * W * sizeof(ST);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -66,7 +85,7 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
     const int ty = blockIdx.x / g.tiles_x;
     const int x0 = tx * TX;                   // first output column
     const int y0 = ty * SOR_TY;               // first output row
-    // box row r <-> grid row y0 - 2 + r; box column k <-> grid column x0 - XH + k
+    // box row r <-> grid row y0 - HR + r; box column k <-> grid column x0 - XH + k
     const int gx = x0 - XH + lane * V;        // grid column of this lane's element 0
 
     if (tid == 0) {
@@ -77,7 +96,7 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
     __syncthreads();
     if (tid == 0) {
         mbar_arrive_expect_tx(&bar, BOX_BYTES);
-        tma_load_3d(box, &tm, x0 - XH, y0 - 2, 0, &bar);
+        tma_load_3d(box, &tm, x0 - XH, y0 - HR, 0, &bar);
     }
     const bool ok = mbar_wait_bounded(&bar, 0, timeout_ns);
     if (!__syncthreads_and(ok)) {
@@ -100,7 +119,7 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
     // (its neighbours have the other colour).
     auto half_sweep = [&](int colour, int r_lo, int r_hi) {
         for (int r = r_lo + warp; r < r_hi; r += SOR_THREADS / 32) {
-            const int y = y0 - 2 + r;
+            const int y = y0 - HR + r;
             if (y < 1 || y > g.R - 2) continue;   // warp-uniform
             ST *row = box + r * W + lane * V;
             CT c[V], n[V], s[V];
@@ -108,8 +127,8 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
             VecIO<ST, V>::load(n, row - W);
             VecIO<ST, V>::load(s, row + W);
             // west of element 0 and east of element V-1 from the neighbouring
-            // lanes (lanes 0 and 31 get stale values: their columns are halo,
-            // beyond the one-cell ring the red sweep needs)
+            // lanes (lanes 0 and 31 get stale values; a half-sweep carries
+            // them one column inward, which the column halo absorbs)
             const CT left = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
             const CT right = __shfl_down_sync(FULL_MASK, c[0], 1);
             // element e has colour (y + gx + e) & 1
@@ -125,19 +144,18 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
             VecIO<ST, V>::store(row, o);
         }
     };
-    // red on the tile and a one-cell ring (box rows 1 .. BY-2), then black on
-    // the tile (box rows 2 .. BY-3)
-    half_sweep(0, 1, SOR_BY - 1);
-    __syncthreads();
-    half_sweep(1, 2, SOR_BY - 2);
-    __syncthreads();
+    // half-sweep h: colour h & 1 (red first) on box rows [1 + h, BY - 1 - h)
+    for (int h = 0; h < n_half; ++h) {
+        half_sweep(h & 1, 1 + h, SOR_BY - 1 - h);
+        __syncthreads();
+    }
 
     // write the tile
     const bool own_cols = lane * V >= XH && lane * V < XH + TX && gx < g.C;
     if (own_cols) {
         const bool full_vec = gx + V <= g.C;
-        for (int r = 2 + warp; r < SOR_BY - 2; r += SOR_THREADS / 32) {
-            const int y = y0 - 2 + r;
+        for (int r = HR + warp; r < HR + SOR_TY; r += SOR_THREADS / 32) {
+            const int y = y0 - HR + r;
             if (y >= g.R) break;
             const ST *row = box + r * W + lane * V;
             ST *q = dst + static_cast<long long>(y) * g.ld + gx;
@@ -157,19 +175,33 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
 // ------------------------------------------------------------------ host -----
 static const void *sor_kernel(int dtype) {
     switch (dtype) {
-        case SDFG_F32: return reinterpret_cast<const void *>(&sor2d_kernel<float, 4>);
-        case SDFG_BF16: return reinterpret_cast<const void *>(&sor2d_kernel<__nv_bfloat16, 4>);
-        default: return reinterpret_cast<const void *>(&sor2d_kernel<double, 2>);
+        case SDFG_F32: return reinterpret_cast<const void *>(&sor2d_kernel<float>);
+        case SDFG_BF16: return reinterpret_cast<const void *>(&sor2d_kernel<__nv_bfloat16>);
+        default: return reinterpret_cast<const void *>(&sor2d_kernel<double>);
     }
 }
 
-static int sor_box_cols(int dtype) { return dtype == SDFG_F64 ? 64 : 128; }
-static int sor_tile_cols(int dtype) { return sor_box_cols(dtype) - 2 * (16 / dtype_bytes(dtype)); }
+template <class ST> static void sor_shape_of(int &ki, int &w, int &tx, int &by) {
+    ki = SorShape<ST>::KI;
+    w = SorShape<ST>::W;
+    tx = SorShape<ST>::TX;
+    by = SorShape<ST>::BY;
+}
+static void sor_shape(int dtype, int &ki, int &w, int &tx, int &by) {
+    switch (dtype) {
+        case SDFG_F32: sor_shape_of<float>(ki, w, tx, by); break;
+        case SDFG_BF16: sor_shape_of<__nv_bfloat16>(ki, w, tx, by); break;
+        default: sor_shape_of<double>(ki, w, tx, by); break;
+    }
+}
 
-static int launch_sor(const CUtensorMap &tm, void *dst, const SorGeo &g, int dtype, double omega, int *err,
-                      cudaStream_t s) {
+static int launch_sor(const CUtensorMap &tm, void *dst, const SorGeo &g, int dtype, double omega, int n_iter,
+                      int *err, cudaStream_t s) {
     const void *fn = sor_kernel(dtype);
-    const size_t smem = static_cast<size_t>(SOR_BY) * sor_box_cols(dtype) * dtype_bytes(dtype);
+    int ki, w, tx, by;
+    sor_shape(dtype, ki, w, tx, by);
+    const size_t smem = static_cast<size_t>(by) * w * dtype_bytes(dtype);
+    int n_half = 2 * n_iter;
     CUtensorMap t = tm;
     SorGeo gg = g;
     void *dp = dst;
@@ -179,8 +211,8 @@ static int launch_sor(const CUtensorMap &tm, void *dst, const SorGeo &g, int dty
     const double ad = 1.0 - omega, bd = 0.25 * omega;
     float af = static_cast<float>(ad), bf = static_cast<float>(bd);
     double a64 = ad, b64 = bd;
-    void *args_f[] = {&t, &dp, &gg, &af, &bf, &err, &to};
-    void *args_d[] = {&t, &dp, &gg, &a64, &b64, &err, &to};
+    void *args_f[] = {&t, &dp, &gg, &af, &bf, &n_half, &err, &to};
+    void *args_d[] = {&t, &dp, &gg, &a64, &b64, &n_half, &err, &to};
     const unsigned blocks = static_cast<unsigned>(static_cast<long long>(g.tiles_x) * ((g.R + SOR_TY - 1) / SOR_TY));
     TimedLaunch tl = stats_begin(FAM_SOR, s);
     cudaError_t e = cudaLaunchKernel(fn, dim3(blocks), dim3(SOR_THREADS), dtype == SDFG_F64 ? args_d : args_f, smem, s);
@@ -214,6 +246,10 @@ extern "C" int sdfg_sor2d(const void *in, void *out, int rows, int cols, int ld,
         return launch_copy2d(out, ld, in, ld, rows, cols, dtype, s);
     }
     const size_t S = dtype_bytes(dtype);
+    int ki, box_cols, tile_cols, box_rows;
+    sor_shape(dtype, ki, box_cols, tile_cols, box_rows);
+    // launches of ki iterations, then one of the remainder
+    const int n_pass = T / ki + (T % ki ? 1 : 0);
     const bool aligned = sor_tma_ok(in, ld, dtype) && sor_tma_ok(out, ld, dtype);
     const int ldw = aligned ? ld : (cols + 31) / 32 * 32;
     const size_t bytes = static_cast<size_t>(rows) * ldw * S;
@@ -224,7 +260,8 @@ extern "C" int sdfg_sor2d(const void *in, void *out, int rows, int cols, int ld,
         rc = scratch_alloc(&a, bytes, s);
         if (rc != SDFG_OK) return rc;
         if (in != out) {
-            first = (T % 2 == 1) ? out : a;
+            // the last pass must land in `out`
+            first = (n_pass % 2 == 1) ? out : a;
             second = first == out ? a : out;
         } else {
             first = a;
@@ -244,28 +281,28 @@ extern "C" int sdfg_sor2d(const void *in, void *out, int rows, int cols, int ld,
         second = a;
     }
     const void *fn = sor_kernel(dtype);
-    const size_t smem = static_cast<size_t>(SOR_BY) * sor_box_cols(dtype) * S;
+    const size_t smem = static_cast<size_t>(box_rows) * box_cols * S;
     static bool attr_done[3] = {false, false, false};
     if (!attr_done[dtype]) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) rc = cuda_error(e, "sor2d attribute");
         else attr_done[dtype] = true;
     }
-    const int box_cols = sor_box_cols(dtype);
     alignas(128) CUtensorMap tm_src0, tm_first, tm_second;
-    if (rc == SDFG_OK) rc = encode_tmap3d(&tm_src0, src0, dtype, 1, rows, cols, ldw, box_cols, SOR_BY);
-    if (rc == SDFG_OK) rc = encode_tmap3d(&tm_first, first, dtype, 1, rows, cols, ldw, box_cols, SOR_BY);
-    if (rc == SDFG_OK) rc = encode_tmap3d(&tm_second, second, dtype, 1, rows, cols, ldw, box_cols, SOR_BY);
+    if (rc == SDFG_OK) rc = encode_tmap3d(&tm_src0, src0, dtype, 1, rows, cols, ldw, box_cols, box_rows);
+    if (rc == SDFG_OK) rc = encode_tmap3d(&tm_first, first, dtype, 1, rows, cols, ldw, box_cols, box_rows);
+    if (rc == SDFG_OK) rc = encode_tmap3d(&tm_second, second, dtype, 1, rows, cols, ldw, box_cols, box_rows);
     SorGeo g;
     g.R = rows;
     g.C = cols;
     g.ld = ldw;
-    g.tiles_x = (cols + sor_tile_cols(dtype) - 1) / sor_tile_cols(dtype);
+    g.tiles_x = (cols + tile_cols - 1) / tile_cols;
     const CUtensorMap *tsrc = &tm_src0;
     void *dst = first;
     void *fin = const_cast<void *>(src0);
-    for (int t = 0; t < T && rc == SDFG_OK; ++t) {
-        rc = launch_sor(*tsrc, dst, g, dtype, omega, st->d_err, s);
+    for (int p = 0; p < n_pass && rc == SDFG_OK; ++p) {
+        const int n_iter = (p < T / ki) ? ki : T % ki;
+        rc = launch_sor(*tsrc, dst, g, dtype, omega, n_iter, st->d_err, s);
         fin = dst;
         tsrc = dst == first ? &tm_first : &tm_second;
         dst = dst == first ? second : first;

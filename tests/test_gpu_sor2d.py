@@ -1,8 +1,9 @@
 """Parity of the red-black SOR path (sdfg_sor2d) with the FP64 oracle.
 
 FP64 is bit-identical (same order of operations); FP32 within 1e-4 and BF16
-within 2e-2 on a smooth field.  Shapes span several tiles (60 rows x 120
-columns for FP32, 60 for FP64, 112 for BF16) with ragged tails, a single
+within 2e-2 on a smooth field.  Shapes span several tiles (60 rows x 112
+columns for FP32, 56 for FP64, 112 for BF16; 4 iterations per launch, 2 for FP64,
+with partial last launches) with ragged tails, a single
 interior point, both colours at the tile edges, several relaxation factors,
 in-place runs, pitched and unaligned layouts and degenerate shapes.  At the
 full 8192^2 size the oracle checks light-cone windows (one iteration moves
