@@ -585,7 +585,8 @@ extern "C" int sdfg_jacobi2d_solve(sdfg_desc *desc, int check_stride, const sdfg
 }
 
 // ---------------------------------------------------------- batch tuner -----
-// Candidates: fused depth k in {4, 8} x segment height in {96, 128, 192}.
+// Candidates: fused depth k in {4, 8} x segment height in {96, 128, 192,
+// 256, 384}.
 // Each is built as a plan over the caller's batch, run once to warm up and
 // once timed; the fastest is cached under the batch's class (dtype, grid
 // count and mean area, both power-of-two buckets) and returned.
@@ -597,7 +598,7 @@ extern "C" int sdfg_autotune_batch(const sdfg_desc *desc, int n, int check_strid
     area /= n;
     const int dtype = desc[0].dtype;
     const int ks[] = {4, 8};
-    const int segs[] = {96, 128, 192};
+    const int segs[] = {96, 128, 192, 256, 384};
     float best_ms = 1e30f;
     sdfg_config winner = {SDFG_KERNEL_PERSISTENT, default_depth(dtype), 96, 4};
     std::vector<sdfg_desc> tmp(desc, desc + n);
