@@ -240,3 +240,54 @@ def test_persistent_single_grid_equals_temporal(shape, T):
             torch.cuda.synchronize()
             assert binding.sdfg_device_error(True) == 0
             assert torch.equal(y, ref)
+
+
+def test_full_512_grid_batch_in_the_bench_configuration():
+    """The benchmark's batch (512 uneven grids, rows and columns log-uniform
+    in [64, 2048], T in [50, 500], each grid pitched to 16-byte rows) in the
+    configuration it measures (one persistent launch, k = 4, 256-row
+    segments, replayed from a plan): every grid runs exactly T steps, and
+    sampled grids across the size range match the FP64 oracle -- small ones
+    whole, large ones on light-cone windows."""
+    import ctypes
+    specs = inputs.batch_specs(512, seed=0)
+    xs, ys, descs = [], [], []
+    for sp in specs:
+        ld = (sp.cols + 3) // 4 * 4
+        x = torch.zeros((sp.rows, ld), device="cuda")[:, :sp.cols]
+        x.copy_(torch.from_numpy(inputs.batch_grid(sp)).float())
+        y = torch.zeros((sp.rows, ld), device="cuda")[:, :sp.cols]
+        xs.append(x)
+        ys.append(y)
+        descs.append(binding.desc_for(x, y, sp.T))
+    L = binding.lib()
+    arr = (binding.sdfg_desc * len(descs))(*descs)
+    cfg = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=4, seg_rows=256, warps=4)
+    plan = ctypes.c_void_p()
+    binding.check(L.sdfg_batch_plan_create(ctypes.byref(plan), arr, len(descs), 64, ctypes.byref(cfg), 0))
+    try:
+        binding.check(L.sdfg_batch_plan_run(plan, torch.cuda.current_stream().cuda_stream))
+        binding.check(L.sdfg_batch_plan_results(plan, arr, len(descs)))
+    finally:
+        binding.check(L.sdfg_batch_plan_destroy(plan))
+    torch.cuda.synchronize()
+    assert binding.sdfg_device_error(True) == 0
+    for d, sp in zip(arr, specs):
+        assert d.status == 0 and d.steps_done == sp.T
+    # samples: the smallest, the largest and a spread in between
+    order = sorted(range(len(specs)), key=lambda g: specs[g].rows * specs[g].cols)
+    picks = [order[0], order[1], order[len(order) // 4], order[len(order) // 2], order[3 * len(order) // 4],
+             order[-2], order[-1]]
+    for g in picks:
+        sp, x, y = specs[g], xs[g], ys[g]
+        xh = h64(x)
+        if sp.rows * sp.cols <= 300_000:
+            want = oracle.jacobi2d(xh, sp.T, threads=0)
+            assert np.abs(h64(y) - want).max() <= TOL[F32], (g, sp)
+        else:
+            R, C = sp.rows, sp.cols
+            for (r0, c0) in [(0, 0), (R // 2, C // 2), (R - 6, C - 6), (R // 3, C - 6)]:
+                r0, c0 = max(0, min(r0, R - 6)), max(0, min(c0, C - 6))
+                want = oracle.jacobi2d_window(xh, sp.T, r0, r0 + 6, c0, c0 + 6, threads=0)
+                got = h64(y[r0:r0 + 6, c0:c0 + 6])
+                assert np.abs(got - want).max() <= TOL[F32], (g, sp, r0, c0)
