@@ -93,3 +93,50 @@ def test_plan_geometry_covers_grid(lib, dtype, k, shape):
 def test_plan_geometry_rejects_bad_depth(lib):
     with pytest.raises(binding.SdfgError):
         binding.sdfg_plan_geometry(64, 64, binding.SDFG_F32, 3, 0)
+
+
+@pytest.mark.parametrize("args", [
+    (1, 1, 8, 8, 8, 8, 5, 7),       # bad dtype
+    (1, 1, -1, 8, 8, 8, 5, 0),      # negative depth
+    (1, 1, 8, 8, 8, 4, 5, 0),       # ld < cols
+    (1, 1, 8, 8, 8, 8, -3, 0),      # negative T
+    (0, 0, 8, 8, 8, 8, 5, 0),       # null pointers with a non-empty box
+])
+def test_host_validation_3d(lib, args):
+    """sdfg_jacobi3d rejects bad arguments before it touches a GPU."""
+    inp, out, D, R, C, ld, T, dt = args
+    rc = lib.sdfg_jacobi3d(4096 if inp else None, 1 << 20 if out else None, D, R, C, ld, T, dt, None)
+    assert rc == binding.SDFG_ERR_INVAL
+    assert binding.last_error()
+
+
+@pytest.mark.parametrize("args", [
+    (1, 1, 8, 8, 8, 5, 1.0, 7),             # bad dtype
+    (1, 1, 8, -2, 8, 5, 1.0, 0),            # negative cols
+    (1, 1, 8, 8, 6, 5, 1.0, 0),             # ld < cols
+    (1, 1, 8, 8, 8, -1, 1.0, 0),            # negative T
+    (1, 1, 8, 8, 8, 5, float("inf"), 0),    # non-finite omega
+    (0, 0, 8, 8, 8, 5, 1.0, 0),             # null pointers with a non-empty grid
+])
+def test_host_validation_sor(lib, args):
+    """sdfg_sor2d rejects bad arguments before it touches a GPU."""
+    inp, out, R, C, ld, T, om, dt = args
+    rc = lib.sdfg_sor2d(4096 if inp else None, 1 << 20 if out else None, R, C, ld, T, om, dt, None)
+    assert rc == binding.SDFG_ERR_INVAL
+    assert binding.last_error()
+
+
+def test_empty_inputs_succeed_without_a_gpu(lib):
+    """Empty boxes and grids are complete no-ops (no device is touched)."""
+    assert lib.sdfg_jacobi3d(None, None, 0, 5, 5, 5, 3, binding.SDFG_F32, None) == binding.SDFG_OK
+    assert lib.sdfg_sor2d(None, None, 0, 5, 5, 3, 1.0, binding.SDFG_F32, None) == binding.SDFG_OK
+
+
+def test_host_validation_laplace1d(lib):
+    """sdfg_laplace1d: negative sizes and a null array are rejected on the
+    host; arrays without an interior point and T = 0 are no-ops."""
+    assert lib.sdfg_laplace1d(None, -1, 5, None) == binding.SDFG_ERR_INVAL
+    assert lib.sdfg_laplace1d(None, 10, -5, None) == binding.SDFG_ERR_INVAL
+    assert lib.sdfg_laplace1d(None, 10, 5, None) == binding.SDFG_ERR_INVAL
+    for N, T in ((0, 5), (2, 5), (10, 0)):
+        assert lib.sdfg_laplace1d(None, N, T, None) == binding.SDFG_OK
