@@ -363,6 +363,18 @@ def run_ours(a):
         assert torch.equal(hy.cuda(), y), "end-to-end result differs from the device-resident result"
     else:
         assert (hy.cuda() - y).abs().max().item() <= 1e-4, "end-to-end result differs from the device-resident result"
+    # the host <-> device copies alone (pinned buffers, the same bytes per step)
+    dbuf = torch.empty_like(x)
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    c0.record(stream)
+    for _ in range(a.steps):
+        dbuf.copy_(hx, non_blocking=True)
+        hy.copy_(dbuf, non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    copy_ms = c0.elapsed_time(c1) / a.steps
 
     if rank != 0:
         if dist is not None:
@@ -410,7 +422,9 @@ def run_ours(a):
                    "l2": "inputs larger than L2 (two 256 MiB grids), no flush", "parallelism": f"replicas{world}"},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": R * C * 4, "d2h_bytes_per_step": R * C * 4},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": R * C * 4, "d2h_bytes_per_step": R * C * 4,
+                "copy_ms_per_step": copy_ms,
+                "copy_gbs": 2 * R * C * 4 / (copy_ms / 1e3) / 1e9 if copy_ms else None},
         "clocks": clk.summary(),
         "gpu_launches": gpu_launches,
     }))
