@@ -112,36 +112,65 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
     for (int e = 0; e < V; ++e)
         if (gx + e >= 1 && gx + e <= g.C - 2) colin |= 1u << e;
     // One half-sweep over box rows [r_lo, r_hi) for the interior points of
-    // colour `colour`, in place.  Every lane computes all V points and keeps
-    // the other colour's values, then writes its V values back as one vector:
-    // points of the other colour are rewritten with the value they already
-    // hold, and a point of this colour is read by no one in this half-sweep
-    // (its neighbours have the other colour).
+    // colour `colour`, in place.  Warp w walks down its own band of
+    // consecutive rows, keeping the north and centre rows in registers and
+    // loading only the south row: a point of this colour is read by no one
+    // in this half-sweep (its neighbours have the other colour), and the
+    // other colour's values -- all that the next row reads from this one --
+    // do not change.  A lane computes the points of this colour among its V
+    // and writes its V values back as one vector (points of the other colour
+    // get the value they already hold).
     auto half_sweep = [&](int colour, int r_lo, int r_hi) {
-        for (int r = r_lo + warp; r < r_hi; r += SOR_THREADS / 32) {
-            const int y = y0 - HR + r;
-            if (y < 1 || y > g.R - 2) continue;   // warp-uniform
+        constexpr int NWARP = SOR_THREADS / 32;
+        const int band = (r_hi - r_lo + NWARP - 1) / NWARP;
+        const int b0 = r_lo + warp * band;
+        const int b1 = min(b0 + band, r_hi);
+        if (b0 >= b1) return;                 // warp-uniform
+        CT n[V], c[V], s[V];
+        VecIO<ST, V>::load(n, box + (b0 - 1) * W + lane * V);
+        VecIO<ST, V>::load(c, box + b0 * W + lane * V);
+        for (int r = b0; r < b1; ++r) {
             ST *row = box + r * W + lane * V;
-            CT c[V], n[V], s[V];
-            VecIO<ST, V>::load(c, row);
-            VecIO<ST, V>::load(n, row - W);
             VecIO<ST, V>::load(s, row + W);
-            // west of element 0 and east of element V-1 from the neighbouring
-            // lanes (lanes 0 and 31 get stale values; a half-sweep carries
-            // them one column inward, which the column halo absorbs)
-            const CT left = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
-            const CT right = __shfl_down_sync(FULL_MASK, c[0], 1);
-            // element e has colour (y + gx + e) & 1
-            const unsigned pick = colin & ((((y + gx + colour) & 1) == 0) ? 0x55555555u : 0xaaaaaaaau);
+            const int y = y0 - HR + r;
+            // element e has colour (y + gx + e) & 1: this row updates
+            // elements e0, e0 + 2, ... (gx is even for every lane, so e0 is
+            // the same across the warp); rows outside the interior keep
+            // their values
+            const bool row_in = y >= 1 && y <= g.R - 2;
+            const int e0 = (y + gx + colour) & 1;
             CT o[V];
 #pragma unroll
-            for (int e = 0; e < V; ++e) {
-                const CT w = e == 0 ? left : c[e - 1];
-                const CT ea = e == V - 1 ? right : c[e + 1];
-                const CT v = sor_point(c[e], n[e], s[e], w, ea, a, b);
-                o[e] = ((pick >> e) & 1u) ? v : c[e];
+            for (int e = 0; e < V; ++e) o[e] = c[e];
+            // west of element 0 (for e0 = 0) or east of element V-1 (for
+            // e0 = 1) from the neighbouring lane; lanes 0 and 31 get stale
+            // values, which a half-sweep carries one column inward and the
+            // column halo absorbs
+            if (e0 == 0) {
+                const CT left = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
+#pragma unroll
+                for (int e = 0; e < V; e += 2) {
+                    const CT w = e == 0 ? left : c[e - 1];
+                    const CT v = sor_point(c[e], n[e], s[e], w, c[e + 1], a, b);
+                    if (row_in && ((colin >> e) & 1u)) o[e] = v;
+                }
+            } else {
+                const CT right = __shfl_down_sync(FULL_MASK, c[0], 1);
+#pragma unroll
+                for (int e = 1; e < V; e += 2) {
+                    const CT ea = e == V - 1 ? right : c[e + 1];
+                    const CT v = sor_point(c[e], n[e], s[e], c[e - 1], ea, a, b);
+                    if (row_in && ((colin >> e) & 1u)) o[e] = v;
+                }
             }
             VecIO<ST, V>::store(row, o);
+            // the next row's north: this row's other-colour values are
+            // unchanged, and its own colour is not read by the next row
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                n[e] = o[e];
+                c[e] = s[e];
+            }
         }
     };
     // half-sweep h: colour h & 1 (red first) on box rows [1 + h, BY - 1 - h)
