@@ -22,6 +22,7 @@
 // Boundary-ring points are copied; every point of the grid is written by
 // exactly one CTA.
 #include <algorithm>
+#include <type_traits>
 #include <math.h>
 
 #include "device_common.cuh"
@@ -120,7 +121,11 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
     // do not change.  A lane computes the points of this colour among its V
     // and writes its V values back as one vector (points of the other colour
     // get the value they already hold).
-    auto half_sweep = [&](int colour, int r_lo, int r_hi) {
+    // EDGE: the tile reaches the grid's first or last row or column, so rows
+    // and columns outside the interior must keep their values; elsewhere
+    // every point in the box is interior and needs no test.
+    auto half_sweep = [&](auto edge_t, int colour, int r_lo, int r_hi) {
+        constexpr bool EDGE = decltype(edge_t)::value;
         constexpr int NWARP = SOR_THREADS / 32;
         const int band = (r_hi - r_lo + NWARP - 1) / NWARP;
         const int b0 = r_lo + warp * band;
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
             // elements e0, e0 + 2, ... (gx is even for every lane, so e0 is
             // the same across the warp); rows outside the interior keep
             // their values
-            const bool row_in = y >= 1 && y <= g.R - 2;
+            const bool row_in = !EDGE || (y >= 1 && y <= g.R - 2);
             const int e0 = (y + gx + colour) & 1;
             CT o[V];
 #pragma unroll
@@ -152,7 +157,7 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
                 for (int e = 0; e < V; e += 2) {
                     const CT w = e == 0 ? left : c[e - 1];
                     const CT v = sor_point(c[e], n[e], s[e], w, c[e + 1], a, b);
-                    if (row_in && ((colin >> e) & 1u)) o[e] = v;
+                    if (!EDGE || (row_in && ((colin >> e) & 1u))) o[e] = v;
                 }
             } else {
                 const CT right = __shfl_down_sync(FULL_MASK, c[0], 1);
@@ -160,7 +165,7 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
                 for (int e = 1; e < V; e += 2) {
                     const CT ea = e == V - 1 ? right : c[e + 1];
                     const CT v = sor_point(c[e], n[e], s[e], c[e - 1], ea, a, b);
-                    if (row_in && ((colin >> e) & 1u)) o[e] = v;
+                    if (!EDGE || (row_in && ((colin >> e) & 1u))) o[e] = v;
                 }
             }
             VecIO<ST, V>::store(row, o);
@@ -174,8 +179,12 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
         }
     };
     // half-sweep h: colour h & 1 (red first) on box rows [1 + h, BY - 1 - h)
+    const bool edge = x0 - XH < 1 || x0 - XH + W > g.C - 1 || y0 - HR < 1 || y0 - HR + SOR_BY > g.R - 1;
     for (int h = 0; h < n_half; ++h) {
-        half_sweep(h & 1, 1 + h, SOR_BY - 1 - h);
+        if (edge)
+            half_sweep(std::true_type(), h & 1, 1 + h, SOR_BY - 1 - h);
+        else
+            half_sweep(std::false_type(), h & 1, 1 + h, SOR_BY - 1 - h);
         __syncthreads();
     }
 
