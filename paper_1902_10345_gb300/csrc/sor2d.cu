@@ -61,6 +61,70 @@ __device__ __forceinline__ double sor_point(double c, double n, double s, double
     return __dadd_rn(__dmul_rn(a, c), __dmul_rn(b, __dadd_rn(__dadd_rn(n, s), __dadd_rn(w, e))));
 }
 
+// Rows of a 4-column-per-lane box (FP32 and BF16 storage) as the half-sweep
+// reads and writes them.  Lane l owns the box columns 4l .. 4l+3; a row with
+// colour parity P updates the lane's elements P and P+2 (one packed FP32x2
+// pair) and only reads the other two.  FP32 rows are kept pair-major: the
+// elements (0, 2) of the 32 lanes fill the row's first 64 floats, the
+// elements (1, 3) the last 64, so a lane loads its row as two 8-byte pairs
+// already paired for the packed arithmetic and stores its two updated points
+// as one conflict-free 8-byte store.  BF16 rows stay in grid order (their
+// conversion to FP32 places the values in any registers).
+template <class ST> struct SorRow4 {  // FP64 (2 columns per lane) never takes this path
+    static constexpr bool PAIR_MAJOR = false;
+    __device__ __forceinline__ static void load(float (&)[4], const ST *, int) {}
+    template <int P> __device__ __forceinline__ static void store_pair(ST *, int, const float (&)[4]) {}
+};
+template <> struct SorRow4<float> {
+    static constexpr bool PAIR_MAJOR = true;
+    __device__ __forceinline__ static void load(float (&x)[4], const float *row, int lane) {
+        const float2 e02 = reinterpret_cast<const float2 *>(row)[lane];
+        const float2 e13 = reinterpret_cast<const float2 *>(row + 64)[lane];
+        x[0] = e02.x; x[2] = e02.y; x[1] = e13.x; x[3] = e13.y;
+    }
+    template <int P> __device__ __forceinline__ static void store_pair(float *row, int lane, const float (&x)[4]) {
+        reinterpret_cast<float2 *>(row + 64 * P)[lane] = make_float2(x[P], x[P + 2]);
+    }
+};
+template <> struct SorRow4<__nv_bfloat16> {
+    static constexpr bool PAIR_MAJOR = false;
+    __device__ __forceinline__ static void load(float (&x)[4], const __nv_bfloat16 *row, int lane) {
+        VecIO<__nv_bfloat16, 4>::load(x, row + 4 * lane);
+    }
+    // the two untouched elements convert back exactly; the updated pair is
+    // rounded to BF16 here
+    template <int P> __device__ __forceinline__ static void store_pair(__nv_bfloat16 *row, int lane, const float (&x)[4]) {
+        VecIO<__nv_bfloat16, 4>::store(row + 4 * lane, x);
+    }
+};
+
+// One row of a half-sweep (V = 4): n, c, s are the rows above, at and below
+// (s is loaded here from `row` + one box row); the elements P, P+2 of c are
+// updated in place and stored.  Same operations, in the same order, as
+// sor_point, two points per packed instruction.
+template <class ST, int P, bool EDGE>
+__device__ __forceinline__ void sor_row4(const float (&n)[4], float (&c)[4], float (&s)[4], ST *row, int lane,
+                                         float a, float b, bool row_in, unsigned colin) {
+    constexpr int W = 128;
+    SorRow4<ST>::load(s, row + W, lane);
+    float2 we;
+    if constexpr (P == 0) {
+        const float left = __shfl_up_sync(FULL_MASK, c[3], 1);
+        we = make_float2(__fadd_rn(left, c[1]), __fadd_rn(c[1], c[3]));
+    } else {
+        const float right = __shfl_down_sync(FULL_MASK, c[0], 1);
+        we = make_float2(__fadd_rn(c[0], c[2]), __fadd_rn(c[2], right));
+    }
+    const float2 ns = __fadd2_rn(make_float2(n[P], n[P + 2]), make_float2(s[P], s[P + 2]));
+    const float2 q = __fadd2_rn(ns, we);
+    const float2 ac = __fmul2_rn(make_float2(a, a), make_float2(c[P], c[P + 2]));
+    const float2 bq = __fmul2_rn(make_float2(b, b), q);
+    const float2 v = __fadd2_rn(ac, bq);
+    if (!EDGE || (row_in && ((colin >> P) & 1u))) c[P] = v.x;
+    if (!EDGE || (row_in && ((colin >> (P + 2)) & 1u))) c[P + 2] = v.y;
+    SorRow4<ST>::template store_pair<P>(row, lane, c);
+}
+
 template <class ST>
 __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constant__ CUtensorMap tm,
                                                             ST *__restrict__ dst, const SorGeo g,
@@ -178,13 +242,79 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
             }
         }
     };
+    // The same half-sweep for 4 columns per lane: a warp's band is walked six
+    // rows at a time, so the three row registers rotate by renaming and the
+    // colour parity of every row (it alternates down the band) is known at
+    // compile time.
+    auto half_sweep4 = [&](auto edge_t, int colour, int r_lo, int r_hi) {
+        constexpr bool EDGE = decltype(edge_t)::value;
+        constexpr int NWARP = SOR_THREADS / 32;
+        const int band = (r_hi - r_lo + NWARP - 1) / NWARP;
+        const int b0 = r_lo + warp * band;
+        const int b1 = min(b0 + band, r_hi);
+        if (b0 >= b1) return;                 // warp-uniform
+        float A[4], B[4], D[4];
+        SorRow4<ST>::load(A, box + (b0 - 1) * W, lane);
+        SorRow4<ST>::load(B, box + b0 * W, lane);
+        const int yb = y0 - HR + b0;          // grid row of box row b0
+        auto rin = [&](int y) { return !EDGE || (y >= 1 && y <= g.R - 2); };
+        auto walk = [&](auto p_t) {
+            constexpr int P = decltype(p_t)::value, Q = 1 - P;
+            int r = b0;
+            ST *row = box + b0 * W;
+            for (; r + 6 <= b1; r += 6, row += 6 * W) {
+                const int y = yb + (r - b0);
+                sor_row4<ST, P, EDGE>(A, B, D, row, lane, a, b, rin(y), colin);
+                sor_row4<ST, Q, EDGE>(B, D, A, row + W, lane, a, b, rin(y + 1), colin);
+                sor_row4<ST, P, EDGE>(D, A, B, row + 2 * W, lane, a, b, rin(y + 2), colin);
+                sor_row4<ST, Q, EDGE>(A, B, D, row + 3 * W, lane, a, b, rin(y + 3), colin);
+                sor_row4<ST, P, EDGE>(B, D, A, row + 4 * W, lane, a, b, rin(y + 4), colin);
+                sor_row4<ST, Q, EDGE>(D, A, B, row + 5 * W, lane, a, b, rin(y + 5), colin);
+            }
+            const int y = yb + (r - b0);
+            if (r >= b1) return;
+            sor_row4<ST, P, EDGE>(A, B, D, row, lane, a, b, rin(y), colin);
+            if (r + 1 >= b1) return;
+            sor_row4<ST, Q, EDGE>(B, D, A, row + W, lane, a, b, rin(y + 1), colin);
+            if (r + 2 >= b1) return;
+            sor_row4<ST, P, EDGE>(D, A, B, row + 2 * W, lane, a, b, rin(y + 2), colin);
+            if (r + 3 >= b1) return;
+            sor_row4<ST, Q, EDGE>(A, B, D, row + 3 * W, lane, a, b, rin(y + 3), colin);
+            if (r + 4 >= b1) return;
+            sor_row4<ST, P, EDGE>(B, D, A, row + 4 * W, lane, a, b, rin(y + 4), colin);
+        };
+        // gx is even for every lane, so the parity is warp-uniform
+        if (((yb + gx + colour) & 1) == 0)
+            walk(std::integral_constant<int, 0>());
+        else
+            walk(std::integral_constant<int, 1>());
+    };
+    if constexpr (V == 4 && SorRow4<ST>::PAIR_MAJOR) {
+        // grid order -> pair-major, one warp per row (all lanes read the row
+        // before any lane writes it)
+        for (int r = warp; r < SOR_BY; r += SOR_THREADS / 32) {
+            CT x[4];
+            VecIO<ST, 4>::load(x, box + r * W + lane * 4);
+            __syncwarp();
+            reinterpret_cast<float2 *>(box + r * W)[lane] = make_float2(x[0], x[2]);
+            reinterpret_cast<float2 *>(box + r * W + 64)[lane] = make_float2(x[1], x[3]);
+        }
+        __syncthreads();
+    }
     // half-sweep h: colour h & 1 (red first) on box rows [1 + h, BY - 1 - h)
     const bool edge = x0 - XH < 1 || x0 - XH + W > g.C - 1 || y0 - HR < 1 || y0 - HR + SOR_BY > g.R - 1;
     for (int h = 0; h < n_half; ++h) {
-        if (edge)
-            half_sweep(std::true_type(), h & 1, 1 + h, SOR_BY - 1 - h);
-        else
-            half_sweep(std::false_type(), h & 1, 1 + h, SOR_BY - 1 - h);
+        if constexpr (V == 4) {
+            if (edge)
+                half_sweep4(std::true_type(), h & 1, 1 + h, SOR_BY - 1 - h);
+            else
+                half_sweep4(std::false_type(), h & 1, 1 + h, SOR_BY - 1 - h);
+        } else {
+            if (edge)
+                half_sweep(std::true_type(), h & 1, 1 + h, SOR_BY - 1 - h);
+            else
+                half_sweep(std::false_type(), h & 1, 1 + h, SOR_BY - 1 - h);
+        }
         __syncthreads();
     }
 
@@ -195,16 +325,18 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
         for (int r = HR + warp; r < HR + SOR_TY; r += SOR_THREADS / 32) {
             const int y = y0 - HR + r;
             if (y >= g.R) break;
-            const ST *row = box + r * W + lane * V;
             ST *q = dst + static_cast<long long>(y) * g.ld + gx;
+            CT v[V];
+            if constexpr (V == 4)
+                SorRow4<ST>::load(v, box + r * W, lane);
+            else
+                VecIO<ST, V>::load(v, box + r * W + lane * V);
             if (full_vec) {
-                CT v[V];
-                VecIO<ST, V>::load(v, row);
                 VecIO<ST, V>::store(q, v);
             } else {
 #pragma unroll
                 for (int e = 0; e < V; ++e)
-                    if (gx + e < g.C) q[e] = row[e];
+                    if (gx + e < g.C) q[e] = static_cast<ST>(v[e]);
             }
         }
     }

@@ -69,6 +69,11 @@ __device__ __forceinline__ void level_row(float (&o)[V], const float (&n)[V], co
     }
 }
 
+// Register pairing of a lane's V = 4 columns in the packed FP32x2 adds: the
+// pairs (0, 1), (2, 3) as a 16-byte load lands them; the pairs (0, 2), (1, 3),
+// which pack one more add; or the first in and the second out.
+constexpr int PAIRS_NATURAL = 0, PAIRS_SPLIT = 1, PAIRS_ENTRY = 2;
+
 // FP32 arithmetic (FP32 and BF16 storage): a fused level carries the UNSCALED
 // 5-point sum, so interior values at level l are 5^l times the state and the
 // factor 0.2^K is applied once, at the last level of the pass.  The row sum
@@ -77,7 +82,7 @@ __device__ __forceinline__ void level_row(float (&o)[V], const float (&n)[V], co
 // multiply.  Boundary cells keep their unscaled value b at every level; a
 // neighbour reads it as 5^l * b (`lscale`), and the last level copies b, so
 // the Dirichlet ring is stored exactly.
-template <int V, bool COLCHK>
+template <int V, bool COLCHK, int PAIRS>
 __device__ __forceinline__ void level_sum(float (&o)[V], const float (&n)[V], const float (&c)[V],
                                           const float (&s)[V], unsigned colmask, float lscale) {
     static_assert(V % 2 == 0, "pairs of columns");
@@ -86,6 +91,33 @@ __device__ __forceinline__ void level_sum(float (&o)[V], const float (&n)[V], co
     for (int e = 0; e < V; ++e) cc[e] = (COLCHK && ((colmask >> e) & 1u)) ? __fmul_rn(c[e], lscale) : c[e];
     const float left = __shfl_up_sync(FULL_MASK, cc[V - 1], 1);
     const float right = __shfl_down_sync(FULL_MASK, cc[0], 1);
+    if constexpr (PAIRS == PAIRS_SPLIT && V == 4) {
+        // The same sums, packed as the column pairs (0, 2) and (1, 3): then
+        // Q = (u0 + u1, u2 + u3) is one FP32x2 add, and every other pair op
+        // is elementwise, so the pairing changes no result.
+        const float2 q = __fadd2_rn(make_float2(cc[0], cc[2]), make_float2(cc[1], cc[3]));
+        const float2 h02 = make_float2(__fadd_rn(left, q.x), __fadd_rn(cc[1], q.y));
+        const float2 h13 = make_float2(__fadd_rn(q.x, cc[2]), __fadd_rn(q.y, right));
+        const float2 ns02 = __fadd2_rn(make_float2(n[0], n[2]), make_float2(s[0], s[2]));
+        const float2 ns13 = __fadd2_rn(make_float2(n[1], n[3]), make_float2(s[1], s[3]));
+        const float2 r02 = __fadd2_rn(h02, ns02);
+        const float2 r13 = __fadd2_rn(h13, ns13);
+        o[0] = r02.x;
+        o[2] = r02.y;
+        o[1] = r13.x;
+        o[3] = r13.y;
+    } else if constexpr (PAIRS == PAIRS_ENTRY && V == 4) {
+        // Rows as a 16-byte load leaves them (pairs (0, 1), (2, 3)) in, the
+        // split pairs out: the last adds are scalar, so no row is re-paired.
+        const float q0 = __fadd_rn(cc[0], cc[1]);
+        const float q1 = __fadd_rn(cc[2], cc[3]);
+        const float2 ns01 = __fadd2_rn(make_float2(n[0], n[1]), make_float2(s[0], s[1]));
+        const float2 ns23 = __fadd2_rn(make_float2(n[2], n[3]), make_float2(s[2], s[3]));
+        o[0] = __fadd_rn(__fadd_rn(left, q0), ns01.x);
+        o[1] = __fadd_rn(__fadd_rn(q0, cc[2]), ns01.y);
+        o[2] = __fadd_rn(__fadd_rn(cc[1], q1), ns23.x);
+        o[3] = __fadd_rn(__fadd_rn(q1, right), ns23.y);
+    } else {
     float h[V];
 #pragma unroll
     for (int p = 0; p < V / 2; ++p) {
@@ -101,6 +133,7 @@ __device__ __forceinline__ void level_sum(float (&o)[V], const float (&n)[V], co
         const float2 r = __fadd2_rn(make_float2(h[2 * p], h[2 * p + 1]), ns);
         o[2 * p] = r.x;
         o[2 * p + 1] = r.y;
+    }
     }
     if (COLCHK) {
 #pragma unroll
@@ -154,10 +187,19 @@ __device__ __noinline__ inline bool drain_after_timeout(uint64_t *bars, uint32_t
 #ifndef SDFG_SCALED_ONE_BODY
 #define SDFG_SCALED_ONE_BODY 1
 #endif
+#ifndef SDFG_SPLIT_PAIRS
+#define SDFG_SPLIT_PAIRS 1
+#endif
 
 template <class ST, int V, int K, bool COLCHK, bool RES, bool EXACT>
 struct UnitPipe {
     using CT = typename Store<ST>::CT;
+    // inner levels pack the column pairs (0, 2), (1, 3); BF16 rows (the
+    // 2-byte type) enter registers through a conversion that can place them
+    // so, FP32 rows as a 16-byte load pairs them and level 0 switches over
+    static constexpr bool SPLIT = SDFG_SPLIT_PAIRS && V == 4;
+    static constexpr int PAIRS0 = !SPLIT ? PAIRS_NATURAL : sizeof(ST) == 2 ? PAIRS_SPLIT : PAIRS_ENTRY;
+    static constexpr int PAIRS1 = SPLIT ? PAIRS_SPLIT : PAIRS_NATURAL;
     static constexpr int W = 32 * V;
     static constexpr uint32_t CHUNK_BYTES = CHUNK_ROWS * W * sizeof(ST);
 
@@ -235,20 +277,27 @@ struct UnitPipe {
             if constexpr (SCALED) {
                 const float LS = 1.0f;  // (no boundary cell inside a scaled unit)
                 // no boundary row or column reaches this unit: one fast sum
-                level_sum<V, false>(o, b[l][SN], b[l][SC], b[l][SS], colmask, LS);
+                if (l == 0)
+                    level_sum<V, false, PAIRS0>(o, b[l][SN], b[l][SC], b[l][SS], colmask, LS);
+                else
+                    level_sum<V, false, PAIRS1>(o, b[l][SN], b[l][SC], b[l][SS], colmask, LS);
                 if (l == K - 1) {
                     // the pass's scale factor 0.2^K, split hi + lo so the product is
                     // rounded once from a ~48-bit factor
                     constexpr double F = pow_fifth(K);
                     constexpr float FHI = static_cast<float>(F);
                     constexpr float FLO = static_cast<float>(F - static_cast<double>(FHI));
+                    // the column pairs level_sum packs
+                    constexpr bool SP = (K == 1 ? PAIRS0 : PAIRS1) != PAIRS_NATURAL;
+                    constexpr int STEP = SP ? V / 2 : 1;
 #pragma unroll
                     for (int p = 0; p < V / 2; ++p) {
-                        const float2 u = make_float2(o[2 * p], o[2 * p + 1]);
+                        const int e0 = SP ? p : 2 * p;
+                        const float2 u = make_float2(o[e0], o[e0 + STEP]);
                         const float2 t = __fmul2_rn(u, make_float2(FLO, FLO));
                         const float2 f = __ffma2_rn(u, make_float2(FHI, FHI), t);
-                        o[2 * p] = f.x;
-                        o[2 * p + 1] = f.y;
+                        o[e0] = f.x;
+                        o[e0 + STEP] = f.y;
                     }
                 }
             } else {
