@@ -12,15 +12,22 @@
 // One launch runs up to KI iterations (2 KI half-sweeps; StateFusion, paper
 // App. B).  A CTA owns a tile of TY rows x TX columns and loads it by 2-D TMA
 // with a halo of 2 KI rows and at least 2 KI columns on each side into shared
-// memory.  Half-sweep h updates, in place, the points of its colour on box
-// rows [1 + h, BY - 1 - h): they read only points of the other colour, none
-// of which change during the half-sweep, and the region shrinks by one row
-// and one column per half-sweep, exactly as far as a half-sweep's values
-// spread.  A barrier separates the half-sweeps.  The tile is then written to
-// the other buffer of a ping-pong pair, so that no CTA reads a value another
-// CTA has already advanced.  The result equals the in-place sweeps.
-// Boundary-ring points are copied; every point of the grid is written by
-// exactly one CTA.
+// memory.  Half-sweep h updates, in place, the points of its colour: they
+// read only points of the other colour, none of which change during the
+// half-sweep.  Values that are wrong for want of a neighbour outside the box
+// spread one row and one column per half-sweep, so after 2 KI half-sweeps the
+// halo has absorbed them.  A barrier separates the half-sweeps.  The tile is
+// then written to the other buffer of a ping-pong pair, so that no CTA reads
+// a value another CTA has already advanced.  The result equals the in-place
+// sweeps.  Boundary-ring points are copied; every point of the grid is
+// written by exactly one CTA.
+//
+// Two kernels.  FP64 storage (2 columns per lane) sweeps the box in shared
+// memory, on box rows [1 + h, BY - 1 - h) in half-sweep h.  FP32 and BF16
+// storage (4 columns per lane) load the box once into registers -- each warp
+// holds a band of SOR_RB consecutive rows for the whole launch -- and pass
+// only the bands' first and last rows through shared memory between
+// half-sweeps.
 #include <algorithm>
 #include <type_traits>
 #include <math.h>
@@ -38,6 +45,9 @@ constexpr int SOR_THREADS = 256;        // 8 warps
 
 // Iterations per launch: 4 for FP32 and BF16 storage (a 16-byte column halo
 // of 8 elements or more), 2 for FP64 (a 32-byte halo of 4 doubles).
+// Rows per warp held in registers by the FP32/BF16 kernel.
+constexpr int SOR_RB = 10;
+
 template <class ST> struct SorShape {
     static constexpr int KI = sizeof(ST) == 8 ? 2 : 4;
     static constexpr int HR = 2 * KI;                         // halo rows (and least halo columns)
@@ -46,7 +56,9 @@ template <class ST> struct SorShape {
     static constexpr int XH = (HR + XA - 1) / XA * XA;        // halo columns
     static constexpr int W = 32 * V;                          // box columns
     static constexpr int TX = W - 2 * XH;                     // output columns per tile
-    static constexpr int BY = SOR_TY + 2 * HR;                // box rows (<= 256: one TMA box)
+    // output rows: FP32/BF16 fill the 8 warps' register bands exactly
+    static constexpr int TY = sizeof(ST) == 8 ? SOR_TY : (SOR_THREADS / 32) * SOR_RB - 2 * HR;
+    static constexpr int BY = TY + 2 * HR;                    // box rows (<= 256: one TMA box)
 };
 
 struct SorGeo {
@@ -59,70 +71,6 @@ __device__ __forceinline__ float sor_point(float c, float n, float s, float w, f
 }
 __device__ __forceinline__ double sor_point(double c, double n, double s, double w, double e, double a, double b) {
     return __dadd_rn(__dmul_rn(a, c), __dmul_rn(b, __dadd_rn(__dadd_rn(n, s), __dadd_rn(w, e))));
-}
-
-// Rows of a 4-column-per-lane box (FP32 and BF16 storage) as the half-sweep
-// reads and writes them.  Lane l owns the box columns 4l .. 4l+3; a row with
-// colour parity P updates the lane's elements P and P+2 (one packed FP32x2
-// pair) and only reads the other two.  FP32 rows are kept pair-major: the
-// elements (0, 2) of the 32 lanes fill the row's first 64 floats, the
-// elements (1, 3) the last 64, so a lane loads its row as two 8-byte pairs
-// already paired for the packed arithmetic and stores its two updated points
-// as one conflict-free 8-byte store.  BF16 rows stay in grid order (their
-// conversion to FP32 places the values in any registers).
-template <class ST> struct SorRow4 {  // FP64 (2 columns per lane) never takes this path
-    static constexpr bool PAIR_MAJOR = false;
-    __device__ __forceinline__ static void load(float (&)[4], const ST *, int) {}
-    template <int P> __device__ __forceinline__ static void store_pair(ST *, int, const float (&)[4]) {}
-};
-template <> struct SorRow4<float> {
-    static constexpr bool PAIR_MAJOR = true;
-    __device__ __forceinline__ static void load(float (&x)[4], const float *row, int lane) {
-        const float2 e02 = reinterpret_cast<const float2 *>(row)[lane];
-        const float2 e13 = reinterpret_cast<const float2 *>(row + 64)[lane];
-        x[0] = e02.x; x[2] = e02.y; x[1] = e13.x; x[3] = e13.y;
-    }
-    template <int P> __device__ __forceinline__ static void store_pair(float *row, int lane, const float (&x)[4]) {
-        reinterpret_cast<float2 *>(row + 64 * P)[lane] = make_float2(x[P], x[P + 2]);
-    }
-};
-template <> struct SorRow4<__nv_bfloat16> {
-    static constexpr bool PAIR_MAJOR = false;
-    __device__ __forceinline__ static void load(float (&x)[4], const __nv_bfloat16 *row, int lane) {
-        VecIO<__nv_bfloat16, 4>::load(x, row + 4 * lane);
-    }
-    // the two untouched elements convert back exactly; the updated pair is
-    // rounded to BF16 here
-    template <int P> __device__ __forceinline__ static void store_pair(__nv_bfloat16 *row, int lane, const float (&x)[4]) {
-        VecIO<__nv_bfloat16, 4>::store(row + 4 * lane, x);
-    }
-};
-
-// One row of a half-sweep (V = 4): n, c, s are the rows above, at and below
-// (s is loaded here from `row` + one box row); the elements P, P+2 of c are
-// updated in place and stored.  Same operations, in the same order, as
-// sor_point, two points per packed instruction.
-template <class ST, int P, bool EDGE>
-__device__ __forceinline__ void sor_row4(const float (&n)[4], float (&c)[4], float (&s)[4], ST *row, int lane,
-                                         float a, float b, bool row_in, unsigned colin) {
-    constexpr int W = 128;
-    SorRow4<ST>::load(s, row + W, lane);
-    float2 we;
-    if constexpr (P == 0) {
-        const float left = __shfl_up_sync(FULL_MASK, c[3], 1);
-        we = make_float2(__fadd_rn(left, c[1]), __fadd_rn(c[1], c[3]));
-    } else {
-        const float right = __shfl_down_sync(FULL_MASK, c[0], 1);
-        we = make_float2(__fadd_rn(c[0], c[2]), __fadd_rn(c[2], right));
-    }
-    const float2 ns = __fadd2_rn(make_float2(n[P], n[P + 2]), make_float2(s[P], s[P + 2]));
-    const float2 q = __fadd2_rn(ns, we);
-    const float2 ac = __fmul2_rn(make_float2(a, a), make_float2(c[P], c[P + 2]));
-    const float2 bq = __fmul2_rn(make_float2(b, b), q);
-    const float2 v = __fadd2_rn(ac, bq);
-    if (!EDGE || (row_in && ((colin >> P) & 1u))) c[P] = v.x;
-    if (!EDGE || (row_in && ((colin >> (P + 2)) & 1u))) c[P + 2] = v.y;
-    SorRow4<ST>::template store_pair<P>(row, lane, c);
 }
 
 template <class ST>
@@ -149,7 +97,7 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
     const int tx = blockIdx.x % g.tiles_x;
     const int ty = blockIdx.x / g.tiles_x;
     const int x0 = tx * TX;                   // first output column
-    const int y0 = ty * SOR_TY;               // first output row
+    const int y0 = ty * SH::TY;               // first output row
     // box row r <-> grid row y0 - HR + r; box column k <-> grid column x0 - XH + k
     const int gx = x0 - XH + lane * V;        // grid column of this lane's element 0
 
@@ -242,79 +190,13 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
             }
         }
     };
-    // The same half-sweep for 4 columns per lane: a warp's band is walked six
-    // rows at a time, so the three row registers rotate by renaming and the
-    // colour parity of every row (it alternates down the band) is known at
-    // compile time.
-    auto half_sweep4 = [&](auto edge_t, int colour, int r_lo, int r_hi) {
-        constexpr bool EDGE = decltype(edge_t)::value;
-        constexpr int NWARP = SOR_THREADS / 32;
-        const int band = (r_hi - r_lo + NWARP - 1) / NWARP;
-        const int b0 = r_lo + warp * band;
-        const int b1 = min(b0 + band, r_hi);
-        if (b0 >= b1) return;                 // warp-uniform
-        float A[4], B[4], D[4];
-        SorRow4<ST>::load(A, box + (b0 - 1) * W, lane);
-        SorRow4<ST>::load(B, box + b0 * W, lane);
-        const int yb = y0 - HR + b0;          // grid row of box row b0
-        auto rin = [&](int y) { return !EDGE || (y >= 1 && y <= g.R - 2); };
-        auto walk = [&](auto p_t) {
-            constexpr int P = decltype(p_t)::value, Q = 1 - P;
-            int r = b0;
-            ST *row = box + b0 * W;
-            for (; r + 6 <= b1; r += 6, row += 6 * W) {
-                const int y = yb + (r - b0);
-                sor_row4<ST, P, EDGE>(A, B, D, row, lane, a, b, rin(y), colin);
-                sor_row4<ST, Q, EDGE>(B, D, A, row + W, lane, a, b, rin(y + 1), colin);
-                sor_row4<ST, P, EDGE>(D, A, B, row + 2 * W, lane, a, b, rin(y + 2), colin);
-                sor_row4<ST, Q, EDGE>(A, B, D, row + 3 * W, lane, a, b, rin(y + 3), colin);
-                sor_row4<ST, P, EDGE>(B, D, A, row + 4 * W, lane, a, b, rin(y + 4), colin);
-                sor_row4<ST, Q, EDGE>(D, A, B, row + 5 * W, lane, a, b, rin(y + 5), colin);
-            }
-            const int y = yb + (r - b0);
-            if (r >= b1) return;
-            sor_row4<ST, P, EDGE>(A, B, D, row, lane, a, b, rin(y), colin);
-            if (r + 1 >= b1) return;
-            sor_row4<ST, Q, EDGE>(B, D, A, row + W, lane, a, b, rin(y + 1), colin);
-            if (r + 2 >= b1) return;
-            sor_row4<ST, P, EDGE>(D, A, B, row + 2 * W, lane, a, b, rin(y + 2), colin);
-            if (r + 3 >= b1) return;
-            sor_row4<ST, Q, EDGE>(A, B, D, row + 3 * W, lane, a, b, rin(y + 3), colin);
-            if (r + 4 >= b1) return;
-            sor_row4<ST, P, EDGE>(B, D, A, row + 4 * W, lane, a, b, rin(y + 4), colin);
-        };
-        // gx is even for every lane, so the parity is warp-uniform
-        if (((yb + gx + colour) & 1) == 0)
-            walk(std::integral_constant<int, 0>());
-        else
-            walk(std::integral_constant<int, 1>());
-    };
-    if constexpr (V == 4 && SorRow4<ST>::PAIR_MAJOR) {
-        // grid order -> pair-major, one warp per row (all lanes read the row
-        // before any lane writes it)
-        for (int r = warp; r < SOR_BY; r += SOR_THREADS / 32) {
-            CT x[4];
-            VecIO<ST, 4>::load(x, box + r * W + lane * 4);
-            __syncwarp();
-            reinterpret_cast<float2 *>(box + r * W)[lane] = make_float2(x[0], x[2]);
-            reinterpret_cast<float2 *>(box + r * W + 64)[lane] = make_float2(x[1], x[3]);
-        }
-        __syncthreads();
-    }
     // half-sweep h: colour h & 1 (red first) on box rows [1 + h, BY - 1 - h)
     const bool edge = x0 - XH < 1 || x0 - XH + W > g.C - 1 || y0 - HR < 1 || y0 - HR + SOR_BY > g.R - 1;
     for (int h = 0; h < n_half; ++h) {
-        if constexpr (V == 4) {
-            if (edge)
-                half_sweep4(std::true_type(), h & 1, 1 + h, SOR_BY - 1 - h);
-            else
-                half_sweep4(std::false_type(), h & 1, 1 + h, SOR_BY - 1 - h);
-        } else {
-            if (edge)
-                half_sweep(std::true_type(), h & 1, 1 + h, SOR_BY - 1 - h);
-            else
-                half_sweep(std::false_type(), h & 1, 1 + h, SOR_BY - 1 - h);
-        }
+        if (edge)
+            half_sweep(std::true_type(), h & 1, 1 + h, SOR_BY - 1 - h);
+        else
+            half_sweep(std::false_type(), h & 1, 1 + h, SOR_BY - 1 - h);
         __syncthreads();
     }
 
@@ -322,54 +204,240 @@ __global__ void __launch_bounds__(SOR_THREADS) sor2d_kernel(const __grid_constan
     const bool own_cols = lane * V >= XH && lane * V < XH + TX && gx < g.C;
     if (own_cols) {
         const bool full_vec = gx + V <= g.C;
-        for (int r = HR + warp; r < HR + SOR_TY; r += SOR_THREADS / 32) {
+        for (int r = HR + warp; r < HR + SH::TY; r += SOR_THREADS / 32) {
             const int y = y0 - HR + r;
             if (y >= g.R) break;
+            const ST *row = box + r * W + lane * V;
             ST *q = dst + static_cast<long long>(y) * g.ld + gx;
-            CT v[V];
-            if constexpr (V == 4)
-                SorRow4<ST>::load(v, box + r * W, lane);
-            else
-                VecIO<ST, V>::load(v, box + r * W + lane * V);
             if (full_vec) {
+                CT v[V];
+                VecIO<ST, V>::load(v, row);
                 VecIO<ST, V>::store(q, v);
             } else {
 #pragma unroll
                 for (int e = 0; e < V; ++e)
-                    if (gx + e < g.C) q[e] = static_cast<ST>(v[e]);
+                    if (gx + e < g.C) q[e] = row[e];
             }
         }
+    }
+}
+
+// ------------------------------------------------- FP32 / BF16 storage ------
+template <int I, int N, class F> __device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>());
+        static_for<I + 1, N>(f);
+    }
+}
+
+// One row of a half-sweep in registers.  Lane l holds the row's columns
+// 4l .. 4l+3 in c; a row of colour parity P updates its elements P and P+2
+// in place from the rows above (n) and below (s) -- of which only elements P
+// and P+2 are read: they have the other colour -- and from c's other two
+// elements.  The same operations, in the same order, as sor_point, two points
+// per packed FP32x2 instruction; BF16 storage rounds the new values to BF16.
+template <bool BF, int P, bool EDGE>
+__device__ __forceinline__ void sor_row_reg(const float (&n)[4], float (&c)[4], const float (&s)[4], float a,
+                                            float b, bool row_in, unsigned colin) {
+    float2 we;
+    if constexpr (P == 0) {
+        const float left = __shfl_up_sync(FULL_MASK, c[3], 1);
+        we = make_float2(__fadd_rn(left, c[1]), __fadd_rn(c[1], c[3]));
+    } else {
+        const float right = __shfl_down_sync(FULL_MASK, c[0], 1);
+        we = make_float2(__fadd_rn(c[0], c[2]), __fadd_rn(c[2], right));
+    }
+    const float2 ns = __fadd2_rn(make_float2(n[P], n[P + 2]), make_float2(s[P], s[P + 2]));
+    const float2 q = __fadd2_rn(ns, we);
+    const float2 ac = __fmul2_rn(make_float2(a, a), make_float2(c[P], c[P + 2]));
+    const float2 bq = __fmul2_rn(make_float2(b, b), q);
+    float2 v = __fadd2_rn(ac, bq);
+    if constexpr (BF) v = __bfloat1622float2(__float22bfloat162_rn(v));
+    if (!EDGE || (row_in && ((colin >> P) & 1u))) c[P] = v.x;
+    if (!EDGE || (row_in && ((colin >> (P + 2)) & 1u))) c[P + 2] = v.y;
+}
+
+// Warp w holds box rows [w RB, w RB + RB) in registers.  Between half-sweeps
+// it publishes its first row to top[w] and its last to bot[w + 1]; in the
+// next half-sweep the row above its band is bot[w] and the row below is
+// top[w + 1].  The slots are pair-major (elements 0 and 2 of the 32 lanes,
+// then elements 1 and 3), and a half-sweep writes only the pair it updated,
+// while the neighbouring warp reads only the other pair (adjacent rows have
+// opposite parity), so one barrier per half-sweep suffices.  bot[0] and
+// top[NW] stand for the rows beyond the box: zeros, whose effect the halo
+// absorbs like any other missing neighbour.
+template <class ST>
+__global__ void __launch_bounds__(SOR_THREADS) sor2d_reg_kernel(const __grid_constant__ CUtensorMap tm,
+                                                                ST *__restrict__ dst, const SorGeo g, float a,
+                                                                float b, int n_half, int *err,
+                                                                unsigned long long timeout_ns) {
+    using SH = SorShape<ST>;
+    constexpr int V = 4;
+    static_assert(SH::V == V, "4 columns per lane");
+    constexpr int W = SH::W;
+    constexpr int XH = SH::XH;
+    constexpr int TX = SH::TX;
+    constexpr int HR = SH::HR;
+    constexpr int TY = SH::TY;
+    constexpr int BY = SH::BY;
+    constexpr int NW = SOR_THREADS / 32;
+    constexpr int RB = SOR_RB;
+    static_assert(BY == NW * RB, "one band of RB rows per warp");
+    constexpr bool BF = sizeof(ST) == 2;
+    constexpr uint32_t BOX_BYTES = BY * W * sizeof(ST);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(16) float top[NW + 1][W];
+    __shared__ __align__(16) float bot[NW + 1][W];
+    ST *box = reinterpret_cast<ST *>(smem_raw);
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int tx = blockIdx.x % g.tiles_x;
+    const int ty = blockIdx.x / g.tiles_x;
+    const int x0 = tx * TX;                   // first output column
+    const int y0 = ty * TY;                   // first output row
+    // box row r <-> grid row y0 - HR + r; box column k <-> grid column x0 - XH + k
+    const int gx = x0 - XH + lane * V;        // grid column of this lane's element 0
+
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        tmap_prefetch(&tm);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar, BOX_BYTES);
+        tma_load_3d(box, &tm, x0 - XH, y0 - HR, 0, &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0, timeout_ns);
+    if (!__syncthreads_and(ok)) {
+        mbar_wait_bounded(&bar, 0, 1000000ull);
+        if (tid == 0) set_device_error(err, DEV_ERR_TIMEOUT_TMA);
+        return;
+    }
+
+    unsigned colin = 0;  // interior columns among this lane's 4
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+        if (gx + e >= 1 && gx + e <= g.C - 2) colin |= 1u << e;
+
+    float X[RB][V];
+    static_for<0, RB>([&](auto i_t) {
+        constexpr int i = decltype(i_t)::value;
+        VecIO<ST, V>::load(X[i], box + (warp * RB + i) * W + lane * V);
+    });
+    auto put = [&](float *slot, const float (&x)[V], int p) {
+        reinterpret_cast<float2 *>(slot + (W / 2) * p)[lane] = make_float2(x[p], x[p + 2]);
+    };
+    put(top[warp], X[0], 0);
+    put(top[warp], X[0], 1);
+    put(bot[warp + 1], X[RB - 1], 0);
+    put(bot[warp + 1], X[RB - 1], 1);
+    if (warp == 0) {
+        reinterpret_cast<float4 *>(bot[0])[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4 *>(top[NW])[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+
+    const int yb = y0 - HR + warp * RB;       // grid row of the band's first row
+    const bool edge = x0 - XH < 1 || x0 - XH + W > g.C - 1 || y0 - HR < 1 || y0 - HR + BY > g.R - 1;
+    // One half-sweep of the band; P is the colour parity of its first row
+    // (rows alternate; gx is even for every lane, so it is warp-uniform).
+    auto sweep = [&](auto p_t, auto edge_t) {
+        constexpr int P = decltype(p_t)::value;
+        constexpr bool EDGE = decltype(edge_t)::value;
+        constexpr int PL = P ^ ((RB - 1) & 1);  // parity of the band's last row
+        float N[V] = {0.f, 0.f, 0.f, 0.f}, S[V] = {0.f, 0.f, 0.f, 0.f};
+        {
+            const float2 t = reinterpret_cast<const float2 *>(bot[warp] + (W / 2) * P)[lane];
+            N[P] = t.x;
+            N[P + 2] = t.y;
+            const float2 u = reinterpret_cast<const float2 *>(top[warp + 1] + (W / 2) * PL)[lane];
+            S[PL] = u.x;
+            S[PL + 2] = u.y;
+        }
+        static_for<0, RB>([&](auto i_t) {
+            constexpr int i = decltype(i_t)::value;
+            const bool row_in = !EDGE || (yb + i >= 1 && yb + i <= g.R - 2);
+            const float(&n)[V] = X[i == 0 ? 0 : i - 1];
+            const float(&s)[V] = X[i == RB - 1 ? RB - 1 : i + 1];
+            if constexpr (i == 0 && RB == 1)
+                sor_row_reg<BF, P, EDGE>(N, X[i], S, a, b, row_in, colin);
+            else if constexpr (i == 0)
+                sor_row_reg<BF, P, EDGE>(N, X[i], s, a, b, row_in, colin);
+            else if constexpr (i == RB - 1)
+                sor_row_reg<BF, P ^ (i & 1), EDGE>(n, X[i], S, a, b, row_in, colin);
+            else
+                sor_row_reg<BF, P ^ (i & 1), EDGE>(n, X[i], s, a, b, row_in, colin);
+        });
+        put(top[warp], X[0], P);
+        put(bot[warp + 1], X[RB - 1], PL);
+    };
+    for (int h = 0; h < n_half; ++h) {
+        const bool p1 = ((yb + gx + (h & 1)) & 1) != 0;
+        if (edge) {
+            if (p1) sweep(std::integral_constant<int, 1>(), std::true_type());
+            else sweep(std::integral_constant<int, 0>(), std::true_type());
+        } else {
+            if (p1) sweep(std::integral_constant<int, 1>(), std::false_type());
+            else sweep(std::integral_constant<int, 0>(), std::false_type());
+        }
+        __syncthreads();
+    }
+
+    // write the tile's rows [HR, HR + TY) straight from registers
+    const bool own_cols = lane * V >= XH && lane * V < XH + TX && gx < g.C;
+    if (own_cols) {
+        const bool full_vec = gx + V <= g.C;
+        static_for<0, RB>([&](auto i_t) {
+            constexpr int i = decltype(i_t)::value;
+            const int r = warp * RB + i;
+            const int y = y0 - HR + r;
+            if (r >= HR && r < HR + TY && y < g.R) {
+                ST *q = dst + static_cast<long long>(y) * g.ld + gx;
+                if (full_vec) {
+                    VecIO<ST, V>::store(q, X[i]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (gx + e < g.C) q[e] = static_cast<ST>(X[i][e]);
+                }
+            }
+        });
     }
 }
 
 // ------------------------------------------------------------------ host -----
 static const void *sor_kernel(int dtype) {
     switch (dtype) {
-        case SDFG_F32: return reinterpret_cast<const void *>(&sor2d_kernel<float>);
-        case SDFG_BF16: return reinterpret_cast<const void *>(&sor2d_kernel<__nv_bfloat16>);
+        case SDFG_F32: return reinterpret_cast<const void *>(&sor2d_reg_kernel<float>);
+        case SDFG_BF16: return reinterpret_cast<const void *>(&sor2d_reg_kernel<__nv_bfloat16>);
         default: return reinterpret_cast<const void *>(&sor2d_kernel<double>);
     }
 }
 
-template <class ST> static void sor_shape_of(int &ki, int &w, int &tx, int &by) {
+template <class ST> static void sor_shape_of(int &ki, int &w, int &tx, int &by, int &ty) {
     ki = SorShape<ST>::KI;
     w = SorShape<ST>::W;
     tx = SorShape<ST>::TX;
     by = SorShape<ST>::BY;
+    ty = SorShape<ST>::TY;
 }
-static void sor_shape(int dtype, int &ki, int &w, int &tx, int &by) {
+static void sor_shape(int dtype, int &ki, int &w, int &tx, int &by, int &ty) {
     switch (dtype) {
-        case SDFG_F32: sor_shape_of<float>(ki, w, tx, by); break;
-        case SDFG_BF16: sor_shape_of<__nv_bfloat16>(ki, w, tx, by); break;
-        default: sor_shape_of<double>(ki, w, tx, by); break;
+        case SDFG_F32: sor_shape_of<float>(ki, w, tx, by, ty); break;
+        case SDFG_BF16: sor_shape_of<__nv_bfloat16>(ki, w, tx, by, ty); break;
+        default: sor_shape_of<double>(ki, w, tx, by, ty); break;
     }
 }
 
 static int launch_sor(const CUtensorMap &tm, void *dst, const SorGeo &g, int dtype, double omega, int n_iter,
                       int *err, cudaStream_t s) {
     const void *fn = sor_kernel(dtype);
-    int ki, w, tx, by;
-    sor_shape(dtype, ki, w, tx, by);
+    int ki, w, tx, by, ty;
+    sor_shape(dtype, ki, w, tx, by, ty);
     const size_t smem = static_cast<size_t>(by) * w * dtype_bytes(dtype);
     int n_half = 2 * n_iter;
     CUtensorMap t = tm;
@@ -383,7 +451,7 @@ static int launch_sor(const CUtensorMap &tm, void *dst, const SorGeo &g, int dty
     double a64 = ad, b64 = bd;
     void *args_f[] = {&t, &dp, &gg, &af, &bf, &n_half, &err, &to};
     void *args_d[] = {&t, &dp, &gg, &a64, &b64, &n_half, &err, &to};
-    const unsigned blocks = static_cast<unsigned>(static_cast<long long>(g.tiles_x) * ((g.R + SOR_TY - 1) / SOR_TY));
+    const unsigned blocks = static_cast<unsigned>(static_cast<long long>(g.tiles_x) * ((g.R + ty - 1) / ty));
     TimedLaunch tl = stats_begin(FAM_SOR, s);
     cudaError_t e = cudaLaunchKernel(fn, dim3(blocks), dim3(SOR_THREADS), dtype == SDFG_F64 ? args_d : args_f, smem, s);
     stats_end(tl, s);
@@ -416,8 +484,8 @@ extern "C" int sdfg_sor2d(const void *in, void *out, int rows, int cols, int ld,
         return launch_copy2d(out, ld, in, ld, rows, cols, dtype, s);
     }
     const size_t S = dtype_bytes(dtype);
-    int ki, box_cols, tile_cols, box_rows;
-    sor_shape(dtype, ki, box_cols, tile_cols, box_rows);
+    int ki, box_cols, tile_cols, box_rows, tile_rows;
+    sor_shape(dtype, ki, box_cols, tile_cols, box_rows, tile_rows);
     // launches of ki iterations, then one of the remainder
     const int n_pass = T / ki + (T % ki ? 1 : 0);
     const bool aligned = sor_tma_ok(in, ld, dtype) && sor_tma_ok(out, ld, dtype);
