@@ -791,12 +791,12 @@ def run_sor(a):
         "dtype": "f32", "data": "synthetic",
         "step_ms": {"median": med_ms, "ci95": ci_ms, "min": min(step_ms), "max": max(step_ms)},
         "config": {"workload": wl, "rows": R, "cols": C, "T": T, "omega": om,
-                   "kernel": "sor2d (4 red-black iterations per launch)", "tile": "60 rows x 112 cols, 4 iterations per launch",
+                   "kernel": "sor2d (4 red-black iterations per launch)", "tile": "64 rows x 112 cols (10 rows per warp in registers), 4 iterations per launch",
                    "l2": "inputs larger than L2 (two 256 MiB grids), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                      "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src,
-                     "kernel": "sor2d_kernel", "k": iters_per_launch,
+                     "kernel": "sor2d_reg_kernel", "k": iters_per_launch,
                      "launches_per_step": n_k / a.steps if n_k else 0,
                      "avg_launch_ms": (ms_k / n_k) if n_k else None,
                      "roofline_gupdates": hbm * iters_per_launch / 8,

@@ -45,11 +45,18 @@ constexpr int SOR_THREADS = 256;        // 8 warps
 
 // Iterations per launch: 4 for FP32 and BF16 storage (a 16-byte column halo
 // of 8 elements or more), 2 for FP64 (a 32-byte halo of 4 doubles).
-// Rows per warp held in registers by the FP32/BF16 kernel.
-constexpr int SOR_RB = 10;
+// Rows per warp held in registers by the FP32/BF16 kernel, and iterations
+// per launch of that kernel.
+#ifndef SDFG_SOR_RB
+#define SDFG_SOR_RB 10
+#endif
+constexpr int SOR_RB = SDFG_SOR_RB;
+#ifndef SDFG_SOR_KI
+#define SDFG_SOR_KI 4
+#endif
 
 template <class ST> struct SorShape {
-    static constexpr int KI = sizeof(ST) == 8 ? 2 : 4;
+    static constexpr int KI = sizeof(ST) == 8 ? 2 : SDFG_SOR_KI;
     static constexpr int HR = 2 * KI;                         // halo rows (and least halo columns)
     static constexpr int V = sizeof(ST) == 8 ? 2 : 4;         // columns per lane
     static constexpr int XA = Store<ST>::xalign;              // TMA x alignment (elements)
@@ -230,12 +237,25 @@ template <int I, int N, class F> __device__ __forceinline__ void static_for(F &&
     }
 }
 
+// Packed FP32x2 add, rounded to nearest.
+__device__ __forceinline__ float2 add2_rn(float2 x, float2 y) {
+    float2 r;
+    asm("{\n\t.reg .b64 a, b, d;\n\t"
+        "mov.b64 a, {%2, %3};\n\t"
+        "mov.b64 b, {%4, %5};\n\t"
+        "add.rn.f32x2 d, a, b;\n\t"
+        "mov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(x.x), "f"(x.y), "f"(y.x), "f"(y.y));
+    return r;
+}
 // One row of a half-sweep in registers.  Lane l holds the row's columns
 // 4l .. 4l+3 in c; a row of colour parity P updates its elements P and P+2
 // in place from the rows above (n) and below (s) -- of which only elements P
 // and P+2 are read: they have the other colour -- and from c's other two
-// elements.  The same operations, in the same order, as sor_point, two points
-// per packed FP32x2 instruction; BF16 storage rounds the new values to BF16.
+// elements.  The same operations, in the same order, as sor_point, each
+// rounded on its own: the sums two points per packed FP32x2 add, the products
+// scalar.  BF16 storage rounds the new values to BF16.
 template <bool BF, int P, bool EDGE>
 __device__ __forceinline__ void sor_row_reg(const float (&n)[4], float (&c)[4], const float (&s)[4], float a,
                                             float b, bool row_in, unsigned colin) {
@@ -247,11 +267,14 @@ __device__ __forceinline__ void sor_row_reg(const float (&n)[4], float (&c)[4], 
         const float right = __shfl_down_sync(FULL_MASK, c[0], 1);
         we = make_float2(__fadd_rn(c[0], c[2]), __fadd_rn(c[2], right));
     }
-    const float2 ns = __fadd2_rn(make_float2(n[P], n[P + 2]), make_float2(s[P], s[P + 2]));
-    const float2 q = __fadd2_rn(ns, we);
-    const float2 ac = __fmul2_rn(make_float2(a, a), make_float2(c[P], c[P + 2]));
-    const float2 bq = __fmul2_rn(make_float2(b, b), q);
-    float2 v = __fadd2_rn(ac, bq);
+    const float2 ns = add2_rn(make_float2(n[P], n[P + 2]), make_float2(s[P], s[P + 2]));
+    const float2 q = add2_rn(ns, we);
+    // the products are scalar: the code generator may fuse a packed product
+    // that has a single use into the packed add consuming it (one rounding
+    // instead of two), even when both carry an explicit rounding mode
+    const float2 ac = make_float2(__fmul_rn(a, c[P]), __fmul_rn(a, c[P + 2]));
+    const float2 bq = make_float2(__fmul_rn(b, q.x), __fmul_rn(b, q.y));
+    float2 v = add2_rn(ac, bq);
     if constexpr (BF) v = __bfloat1622float2(__float22bfloat162_rn(v));
     if (!EDGE || (row_in && ((colin >> P) & 1u))) c[P] = v.x;
     if (!EDGE || (row_in && ((colin >> (P + 2)) & 1u))) c[P + 2] = v.y;

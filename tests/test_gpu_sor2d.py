@@ -1,9 +1,9 @@
 """Parity of the red-black SOR path (sdfg_sor2d) with the FP64 oracle.
 
 FP64 is bit-identical (same order of operations); FP32 within 1e-4 and BF16
-within 2e-2 on a smooth field.  Shapes span several tiles (60 rows x 112
-columns for FP32, 56 for FP64, 112 for BF16; 4 iterations per launch, 2 for FP64,
-with partial last launches) with ragged tails, a single
+within 2e-2 on a smooth field.  Shapes span several tiles (64 rows x 112
+columns for FP32 and BF16, 60 x 56 for FP64; 4 iterations per launch, 2 for
+FP64, with partial last launches) with ragged tails, a single
 interior point, both colours at the tile edges, several relaxation factors,
 in-place runs, pitched and unaligned layouts and degenerate shapes.  At the
 full 8192^2 size the oracle checks light-cone windows (one iteration moves
@@ -81,6 +81,60 @@ def test_bf16_smooth_field():
     g = inputs.sinusoid_field(n, seed=2, k_max=1)[:250, :300]
     x = torch.from_numpy(np.ascontiguousarray(g)).to(torch.bfloat16).cuda()
     check(run(x, 10, 1.0), x, 10, 1.0, BF16)
+
+
+@pytest.mark.parametrize("shape", [(90, 250), (203, 97), (66, 113)])
+@pytest.mark.parametrize("T,omega", [(3, 1.5), (4, 1.9)])
+def test_bf16_tiles_and_relaxation(shape, T, omega):
+    """BF16 storage across several tiles (64 rows x 112 columns) with ragged
+    edges and partial last launches: every update is rounded to BF16, so the
+    result follows the FP64 oracle within 2e-2 on a smooth field."""
+    R, C = shape
+    g = inputs.sinusoid_field(max(R, C), seed=R + C, k_max=1)[:R, :C]
+    x = torch.from_numpy(np.ascontiguousarray(g)).to(torch.bfloat16).cuda()
+    check(run(x, T, omega), x, T, omega, BF16)
+
+
+def _bf16_rne(x):
+    """float32 -> nearest BF16 (ties to even), returned as float32."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    return (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16).astype(np.uint32).view(np.float32)
+
+
+def _sor_fp32_order(g32, T, omega, bf16=False):
+    """Red-black SOR in float32 with every operation rounded on its own, in
+    the order the FP32 path states: q = (n + s) + (w + e), then
+    (1 - omega) * c + (omega / 4) * q, with the two coefficients rounded from
+    double once; BF16 storage rounds each new value to BF16."""
+    A = np.array(g32, dtype=np.float32)
+    R, C = A.shape
+    a, b = np.float32(1.0 - omega), np.float32(0.25 * omega)
+    for _ in range(T):
+        for colour in (0, 1):
+            for i in range(1, R - 1):
+                js = np.arange(1 + ((i + 1 + colour) & 1), C - 1, 2)
+                q = (A[i - 1, js] + A[i + 1, js]) + (A[i, js - 1] + A[i, js + 1])
+                v = a * A[i, js] + b * q
+                A[i, js] = _bf16_rne(v) if bf16 else v
+    return A
+
+
+@pytest.mark.parametrize("dt", [F32, BF16])
+@pytest.mark.parametrize("shape", [(37, 130), (150, 60)])
+def test_fp32_operation_order_bitwise(shape, dt):
+    """The FP32 arithmetic (FP32 and BF16 storage) is exactly the stated
+    sequence of separately rounded operations: no multiply is fused with an
+    add.  Checked bit for bit against that sequence in numpy, across tile
+    edges and a partial last launch (T = 6)."""
+    T, om = 6, 1.7
+    g = np.random.default_rng(sum(shape)).random(shape)
+    x = torch.from_numpy(g).float().cuda()
+    if dt == BF16:
+        x = x.to(torch.bfloat16)
+    want = _sor_fp32_order(x.float().cpu().numpy(), T, om, bf16=(dt == BF16))
+    got = run(x, T, om).float().cpu().numpy()
+    diff = got != want
+    assert not diff.any(), (int(diff.sum()), float(np.abs(got - want).max()), np.argwhere(diff)[:4].tolist())
 
 
 def test_in_place_odd_and_even_T():
