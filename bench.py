@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--k", type=int, default=0, help="fused depth (0 = library default / autotuned)")
     p.add_argument("--warps", type=int, default=0)
     p.add_argument("--seg-rows", type=int, default=0)
-    p.add_argument("--kernel", choices=["persistent", "temporal"], default="persistent")
+    p.add_argument("--kernel", choices=["persistent", "temporal", "resident"], default="persistent")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--workload", choices=["single", "batch", "precision", "serve", "paper", "3d", "sor"],
@@ -168,6 +168,12 @@ def committed_traffic(kernel_digest: str, workload: str):
         if m_d and m_w and m_t and m_d.group(1) == kernel_digest and m_w.group(1) == workload:
             return float(m_t.group(1))
     return None
+
+
+def kernel_code(binding, name: str) -> int:
+    """The library's kernel-family code for a --kernel name."""
+    return {"persistent": binding.SDFG_KERNEL_PERSISTENT, "temporal": binding.SDFG_KERNEL_TEMPORAL,
+            "resident": binding.SDFG_KERNEL_RESIDENT}[name]
 
 
 # ------------------------------------------------------------ CPU oracle -------
@@ -308,8 +314,8 @@ def run_ours(a):
     x = torch.from_numpy(g).float().cuda()
     y = torch.empty_like(x)
     # the launch configuration timed here (and used by the full-size parity test)
-    cfg = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT if a.kernel == "persistent" else
-                         binding.SDFG_KERNEL_TEMPORAL, k=a.k or 8, seg_rows=a.seg_rows or 128, warps=a.warps or 4)
+    cfg = binding.config(kernel=kernel_code(binding, a.kernel), k=a.k or 8, seg_rows=a.seg_rows or 128,
+                         warps=a.warps or 4)
     stream = torch.cuda.current_stream()
     updates = (R - 2) * (C - 2) * T
 
@@ -333,7 +339,7 @@ def run_ours(a):
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
     med_ms, ci_ms = median_ci95(step_ms)
     launches = {}
-    for fam in ("naive", "temporal", "persistent", "reduce", "copy", "stencil3d", "sor"):
+    for fam in ("naive", "temporal", "persistent", "reduce", "copy", "stencil3d", "sor", "resident"):
         launches[fam] = binding.sdfg_stats_get(fam)
     binding.sdfg_stats_reset()
     binding.check(binding.sdfg_device_error(True))
@@ -383,7 +389,7 @@ def run_ours(a):
 
     # roofline of the dominant kernel: algorithmic bytes = interior points x
     # 2 x 4 B per pass (one read + one write per pass of k fused steps)
-    fam = max(("temporal", "persistent"), key=lambda f: launches[f][1])
+    fam = max(("temporal", "persistent", "resident"), key=lambda f: launches[f][1])
     n_tp, ms_tp = launches[fam]
     hbm, hbm_src = measured_peaks()
     k_used = cfg.k
@@ -588,9 +594,9 @@ def run_paper(a):
     x = torch.from_numpy(g).float().cuda()
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
-    if a.k or a.seg_rows:
-        cfg = binding.config(kernel=binding.SDFG_KERNEL_TEMPORAL if a.kernel == "temporal" else
-                             binding.SDFG_KERNEL_PERSISTENT, k=a.k or 8, seg_rows=a.seg_rows, warps=a.warps or 4)
+    if a.k or a.seg_rows or a.kernel != "persistent":
+        cfg = binding.config(kernel=kernel_code(binding, a.kernel), k=a.k or 8, seg_rows=a.seg_rows,
+                             warps=a.warps or 4)
     else:
         cfg = binding.sdfg_autotune(R, C, T, binding.SDFG_F32, stream.cuda_stream)
     for _ in range(max(3, a.warmup)):

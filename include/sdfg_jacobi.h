@@ -77,7 +77,12 @@ typedef enum {
     SDFG_KERNEL_AUTO = 0,       /* autotuned choice                          */
     SDFG_KERNEL_NAIVE = 1,      /* one timestep per launch, one thread/point */
     SDFG_KERNEL_TEMPORAL = 2,   /* k timesteps per launch (one pass)         */
-    SDFG_KERNEL_PERSISTENT = 3  /* one launch for all passes, dependency-driven */
+    SDFG_KERNEL_PERSISTENT = 3, /* one launch for all passes, dependency-driven */
+    SDFG_KERNEL_RESIDENT = 4    /* k timesteps per launch, each CTA's 256 x 112
+                                   tile held in registers (FP32/BF16 storage;
+                                   FP64 runs the temporal kernel instead);
+                                   for grids that fit in L2, where a pass is
+                                   latency-bound                            */
 } sdfg_kernel;
 
 /*

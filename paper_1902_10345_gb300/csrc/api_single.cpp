@@ -38,7 +38,7 @@ int validate_grid(const void *in, const void *out, int R, int C, int ld, long lo
 int resolve_config(const sdfg_config *cfg, int R, int C, int dtype, sdfg_config *out) {
     sdfg_config c = {SDFG_KERNEL_AUTO, 0, 0, 0};
     if (cfg) c = *cfg;
-    if (c.kernel < SDFG_KERNEL_AUTO || c.kernel > SDFG_KERNEL_PERSISTENT)
+    if (c.kernel < SDFG_KERNEL_AUTO || c.kernel > SDFG_KERNEL_RESIDENT)
         return set_error(SDFG_ERR_INVAL, "unknown kernel family %d", c.kernel);
     if (c.k != 0 && !depth_supported(c.k)) return set_error(SDFG_ERR_INVAL, "k=%d not supported (1, 2, 4, 8)", c.k);
     if (c.seg_rows < 0 || c.warps < 0 || c.warps > MAX_WARPS)
@@ -64,6 +64,7 @@ static int run_pass_sequence(const void *src0, void *first, void *second, const 
                              void **final) {
     *final = const_cast<void *>(src0);
     if (ks.empty()) return SDFG_OK;
+    if (c.kernel == SDFG_KERNEL_RESIDENT) return run_resident_passes(src0, first, second, ks, R, C, ld, dtype, st, s, final);
     if (c.kernel == SDFG_KERNEL_NAIVE) {
         const void *src = src0;
         void *dst = first;
@@ -206,6 +207,7 @@ int run_single(const void *in, void *out, int R, int C, int ld, long long T, int
         return run_single_persistent(in, out, R, C, ld, T, dtype, pc, st, s);
     }
     if (c.kernel == SDFG_KERNEL_PERSISTENT) c.kernel = SDFG_KERNEL_TEMPORAL;
+    if (c.kernel == SDFG_KERNEL_RESIDENT && !resident_supported(dtype)) c.kernel = SDFG_KERNEL_TEMPORAL;
 
     if (c.kernel != SDFG_KERNEL_NAIVE && !tma_ok) {
         // stage through two aligned pitched grids

@@ -111,6 +111,9 @@ extern "C" int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *
     const int segs_c[] = {24, 48, 96, 128, 192};
     float best_ms = 1e30f;
     sdfg_config winner = {SDFG_KERNEL_TEMPORAL, default_depth(dtype), 0, 4};
+    // the register-resident pass is a candidate where both grids fit in L2
+    // (there a pass is latency-bound, which is what it shortens)
+    const bool try_resident = resident_supported(dtype) && 2 * bytes <= (96ull << 20);
     for (int k : ks) {
         for (int kern : kernels) {
             for (int sr : segs_c) {
@@ -137,6 +140,24 @@ extern "C" int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *
             if (rc != SDFG_OK) break;
         }
         if (rc != SDFG_OK) break;
+        if (try_resident) {
+            sdfg_config c = {SDFG_KERNEL_RESIDENT, k, 0, 0};
+            rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);
+            if (rc == SDFG_OK) {
+                cudaEventRecord(e0, s);
+                rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);
+                cudaEventRecord(e1, s);
+            }
+            if (rc == SDFG_OK && cudaEventSynchronize(e1) != cudaSuccess)
+                rc = cuda_error(cudaGetLastError(), "autotune sync");
+            if (rc != SDFG_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                winner = c;
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -76,7 +76,17 @@ struct TimedLaunch {
     int family = -1;
     bool active() const { return family >= 0; }
 };
-enum Family { FAM_NAIVE = 0, FAM_TEMPORAL, FAM_PERSISTENT, FAM_REDUCE, FAM_COPY, FAM_STENCIL3D, FAM_SOR, FAM_COUNT };
+enum Family {
+    FAM_NAIVE = 0,
+    FAM_TEMPORAL,
+    FAM_PERSISTENT,
+    FAM_REDUCE,
+    FAM_COPY,
+    FAM_STENCIL3D,
+    FAM_SOR,
+    FAM_RESIDENT,
+    FAM_COUNT
+};
 TimedLaunch stats_begin(int family, cudaStream_t s);
 // No launch is timed on this thread while suspended (stream capture).
 void stats_suspend(bool on);
@@ -93,5 +103,12 @@ int launch_temporal_pass(const CUtensorMap *tm_src, void *dst, const GridGeo &g,
 int temporal_blocks_per_sm(int dtype, int k, int warps);
 size_t temporal_smem_bytes(int dtype, int warps);
 int launch_copy2d(void *dst, int ld_dst, const void *src, int ld_src, int rows, int cols, int dtype, cudaStream_t s);
+
+// ---- register-resident passes (resident.cu) ----------------------------------
+bool resident_supported(int dtype);
+// The passes `ks` (each 1..8 steps) from src0, alternating between `first`
+// and `second`; *final receives the buffer holding the result.
+int run_resident_passes(const void *src0, void *first, void *second, const std::vector<int> &ks, int R, int C,
+                        int ld, int dtype, DeviceState *st, cudaStream_t s, void **final);
 
 }  // namespace sdfg
