@@ -61,13 +61,15 @@ def _digest() -> str:
 KERNEL_FILES = ["device_common.cuh", "temporal_unit.cuh", "geometry.h", "persistent.h", "persistent.cu", "kernels.cu"]
 KERNEL_FILES_3D = ["device_common.cuh", "jacobi3d.cu"]
 KERNEL_FILES_SOR = ["device_common.cuh", "sor2d.cu"]
+KERNEL_FILES_RESIDENT = ["device_common.cuh", "resident.cu"]
 
 
 def kernel_digest(files=None) -> str:
     """Digest of the device sources and flags that define the kernels (used
     to tell whether a committed profile still describes the current kernels);
-    files: the 2-D kernels' sources by default, KERNEL_FILES_3D or
-    KERNEL_FILES_SOR for the 3-D and SOR ones."""
+    files: the 2-D kernels' sources by default, KERNEL_FILES_3D,
+    KERNEL_FILES_SOR or KERNEL_FILES_RESIDENT for the 3-D, SOR and
+    register-resident ones."""
     h = hashlib.sha256()
     for f in files or KERNEL_FILES:
         with open(os.path.join(CSRC, f), "rb") as fh:

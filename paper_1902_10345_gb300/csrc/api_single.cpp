@@ -195,8 +195,10 @@ int run_single(const void *in, void *out, int R, int C, int ld, long long T, int
     sdfg_config c;
     rc = resolve_config(cfg, R, C, dtype, &c);
     if (rc != SDFG_OK) return rc;
-    const std::vector<int> ks = c.kernel == SDFG_KERNEL_NAIVE ? std::vector<int>(1, static_cast<int>(T))
-                                                              : plan_passes(T, c.k);
+    if (c.kernel == SDFG_KERNEL_RESIDENT && !resident_supported(dtype)) c.kernel = SDFG_KERNEL_TEMPORAL;
+    const std::vector<int> ks = c.kernel == SDFG_KERNEL_NAIVE      ? std::vector<int>(1, static_cast<int>(T))
+                                : c.kernel == SDFG_KERNEL_RESIDENT ? plan_resident_passes(T, c.k)
+                                                                   : plan_passes(T, c.k);
     const long long n_steps_total = c.kernel == SDFG_KERNEL_NAIVE ? T : static_cast<long long>(ks.size());
     const int S = dtype_bytes(dtype);
     const bool tma_ok = tma_compatible(in, ld, dtype) && tma_compatible(out, ld, dtype);
@@ -207,7 +209,6 @@ int run_single(const void *in, void *out, int R, int C, int ld, long long T, int
         return run_single_persistent(in, out, R, C, ld, T, dtype, pc, st, s);
     }
     if (c.kernel == SDFG_KERNEL_PERSISTENT) c.kernel = SDFG_KERNEL_TEMPORAL;
-    if (c.kernel == SDFG_KERNEL_RESIDENT && !resident_supported(dtype)) c.kernel = SDFG_KERNEL_TEMPORAL;
 
     if (c.kernel != SDFG_KERNEL_NAIVE && !tma_ok) {
         // stage through two aligned pitched grids

@@ -240,6 +240,14 @@ static const void *resident_kernel(int dtype) {
 
 bool resident_supported(int dtype) { return dtype == SDFG_F32 || dtype == SDFG_BF16; }
 
+std::vector<int> plan_resident_passes(long long T, int k) {
+    std::vector<int> p;
+    if (T <= 0 || k < 1) return p;
+    p.assign(static_cast<size_t>(T / k), k);
+    if (T % k) p.push_back(static_cast<int>(T % k));
+    return p;
+}
+
 int run_resident_passes(const void *src0, void *first, void *second, const std::vector<int> &ks, int R, int C,
                         int ld, int dtype, DeviceState *st, cudaStream_t s, void **final) {
     *final = const_cast<void *>(src0);

@@ -106,6 +106,8 @@ int launch_copy2d(void *dst, int ld_dst, const void *src, int ld_src, int rows, 
 
 // ---- register-resident passes (resident.cu) ----------------------------------
 bool resident_supported(int dtype);
+// T steps as passes of k (1..8) and one pass for the remainder.
+std::vector<int> plan_resident_passes(long long T, int k);
 // The passes `ks` (each 1..8 steps) from src0, alternating between `first`
 // and `second`; *final receives the buffer holding the result.
 int run_resident_passes(const void *src0, void *first, void *second, const std::vector<int> &ks, int R, int C,
