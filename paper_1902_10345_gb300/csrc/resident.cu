@@ -9,7 +9,8 @@
 // speed.  Here a CTA of 16 warps loads its box with two TMA copies, each warp
 // takes a band of 17 consecutive box rows into registers, and all bands
 // advance together, one barrier per step, so a pass costs one box load, k
-// steps of arithmetic from registers and one store.
+// steps of arithmetic from registers and one store, and consecutive passes
+// overlap their launch with the previous pass's end.
 //
 // Geometry: the box is 272 rows x 128 columns; the tile it updates is the
 // 256 x 112 interior of the box (8 halo rows and columns on each side).  A
@@ -45,6 +46,14 @@ constexpr int RS_TY = RS_BY - 2 * RS_HALO;      // 256 output rows per tile
 constexpr int RS_W = 128;                       // box columns, 4 per lane
 constexpr int RS_TX = RS_W - 2 * RS_HALO;       // 112 output columns per tile
 constexpr int RS_BOX_ROWS = RS_BY / 2;          // rows per TMA copy (<= 256)
+
+// Passes are launched as programmatic dependents of the previous pass: the
+// next launch is scheduled as soon as every CTA of this one has started, and
+// its prologue (barrier setup, descriptor prefetch) runs while this pass
+// finishes; it reads the grid only after this pass has completed.
+#ifndef SDFG_RESIDENT_PDL
+#define SDFG_RESIDENT_PDL 1
+#endif
 
 struct ResGeo {
     int R, C, ld;
@@ -106,6 +115,12 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
         reinterpret_cast<float4 *>(top[0][RS_NW])[lane] = z;
         reinterpret_cast<float4 *>(top[1][RS_NW])[lane] = z;
     }
+#if SDFG_RESIDENT_PDL
+    // the next pass may launch now; this one reads the previous pass's output
+    // only after that pass has completed and its writes are visible
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
     __syncthreads();
     if (tid == 0) {
         mbar_arrive_expect_tx(&bar, BOX_BYTES);
@@ -285,7 +300,21 @@ int run_resident_passes(const void *src0, void *first, void *second, const std::
         int k = ks[p];
         void *args[] = {&t, &dp, &g, &k, &err, &to};
         TimedLaunch tl = stats_begin(FAM_RESIDENT, s);
+#if SDFG_RESIDENT_PDL
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(blocks);
+        lc.blockDim = dim3(RS_THREADS);
+        lc.dynamicSmemBytes = smem;
+        lc.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelExC(&lc, fn, args);
+#else
         const cudaError_t e = cudaLaunchKernel(fn, dim3(blocks), dim3(RS_THREADS), args, smem, s);
+#endif
         stats_end(tl, s);
         if (e != cudaSuccess) return cuda_error(e, "resident launch");
         *final = dst;
