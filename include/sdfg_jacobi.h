@@ -287,7 +287,11 @@ int sdfg_sor2d(const void *in, void *out, int rows, int cols, int ld, int T, dou
                void *stream);
 
 /* Autotuner: times candidate configurations for this shape and dtype on the
- * calling stream, caches the best by shape class, and returns it. */
+ * calling stream (min(T, 64) steps each: the streamed and persistent kernels
+ * at k = 2, 4, 8 and several segment heights, plus the register-resident
+ * kernel at k = 2, 4, 8 for FP32/BF16 grids whose two buffers fit in
+ * 96 MiB), caches the best by shape class, and returns it.  Allocates two
+ * scratch grids for the trials and frees them. */
 int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *best, void *stream);
 
 /* Batch autotuner: times candidate (k, segment height) plans of the
