@@ -361,11 +361,12 @@ def run_ours(a):
     e2e_max = max_over_ranks(e2e_s, dist, "cuda")
     e2e_value = aggregate_rate(updates * a.steps, world, e2e_max) / 1e9
     # the host entry point runs the library's default geometry (k = 8,
-    # 128-row segments): FP32 results depend only on k and the segment height
-    # (they decide which units keep the exact summation order), so the two are
-    # bitwise equal for that geometry and agree to the FP32 parity tolerance
-    # otherwise
-    if (cfg.k, cfg.seg_rows) == (8, 128):
+    # 128-row segments): FP32 results of the streamed and persistent kernels
+    # depend only on k and the segment height (they decide which units keep
+    # the exact summation order), so the two are bitwise equal for that
+    # geometry and agree to the FP32 parity tolerance otherwise (as does the
+    # register-resident kernel, which keeps the exact order everywhere)
+    if a.kernel != "resident" and (cfg.k, cfg.seg_rows) == (8, 128):
         assert torch.equal(hy.cuda(), y), "end-to-end result differs from the device-resident result"
     else:
         assert (hy.cuda() - y).abs().max().item() <= 1e-4, "end-to-end result differs from the device-resident result"
