@@ -25,6 +25,7 @@ import os
 import re
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -47,7 +48,7 @@ def parse():
     p.add_argument("--k", type=int, default=0, help="fused depth (0 = library default / autotuned)")
     p.add_argument("--warps", type=int, default=0)
     p.add_argument("--seg-rows", type=int, default=0)
-    p.add_argument("--kernel", choices=["persistent", "temporal", "resident"], default="persistent")
+    p.add_argument("--kernel", choices=["persistent", "temporal", "resident", "skewed"], default="persistent")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--workload", choices=["single", "batch", "precision", "serve", "paper", "3d", "sor"],
@@ -101,7 +102,7 @@ CLOCK_FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_eve
 class ClockSampler:
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"sdfg_bench_clocks_{os.getpid()}.csv")
         self.gpu = gpu_index
 
     def __enter__(self):
@@ -173,7 +174,7 @@ def committed_traffic(kernel_digest: str, workload: str):
 def kernel_code(binding, name: str) -> int:
     """The library's kernel-family code for a --kernel name."""
     return {"persistent": binding.SDFG_KERNEL_PERSISTENT, "temporal": binding.SDFG_KERNEL_TEMPORAL,
-            "resident": binding.SDFG_KERNEL_RESIDENT}[name]
+            "resident": binding.SDFG_KERNEL_RESIDENT, "skewed": binding.SDFG_KERNEL_SKEWED}[name]
 
 
 # ------------------------------------------------------------ CPU oracle -------
@@ -314,8 +315,8 @@ def run_ours(a):
     x = torch.from_numpy(g).float().cuda()
     y = torch.empty_like(x)
     # the launch configuration timed here (and used by the full-size parity test)
-    cfg = binding.config(kernel=kernel_code(binding, a.kernel), k=a.k or 8, seg_rows=a.seg_rows or 128,
-                         warps=a.warps or 4)
+    cfg = binding.config(kernel=kernel_code(binding, a.kernel), k=a.k or 8,
+                         seg_rows=a.seg_rows or (1024 if a.kernel == "skewed" else 128), warps=a.warps or 4)
     stream = torch.cuda.current_stream()
     updates = (R - 2) * (C - 2) * T
 
@@ -339,7 +340,7 @@ def run_ours(a):
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
     med_ms, ci_ms = median_ci95(step_ms)
     launches = {}
-    for fam in ("naive", "temporal", "persistent", "reduce", "copy", "stencil3d", "sor", "resident"):
+    for fam in ("naive", "temporal", "persistent", "reduce", "copy", "stencil3d", "sor", "resident", "skewed"):
         launches[fam] = binding.sdfg_stats_get(fam)
     binding.sdfg_stats_reset()
     binding.check(binding.sdfg_device_error(True))
@@ -390,12 +391,12 @@ def run_ours(a):
 
     # roofline of the dominant kernel: algorithmic bytes = interior points x
     # 2 x 4 B per pass (one read + one write per pass of k fused steps)
-    fam = max(("temporal", "persistent", "resident"), key=lambda f: launches[f][1])
+    fam = max(("temporal", "persistent", "resident", "skewed"), key=lambda f: launches[f][1])
     n_tp, ms_tp = launches[fam]
     hbm, hbm_src = measured_peaks()
     k_used = cfg.k
     passes_per_step = -(-T // k_used)
-    bytes_per_launch = (R - 2) * (C - 2) * 2 * 4 * (passes_per_step if fam == "persistent" else 1)
+    bytes_per_launch = (R - 2) * (C - 2) * 2 * 4 * (passes_per_step if fam in ("persistent", "skewed") else 1)
     achieved = bytes_per_launch / (ms_tp / n_tp / 1e3) / 1e9 if n_tp else None
     # FP32-pipe ceiling: 5 FP32 lane-ops per update on 152 SMs x 128 lanes at the max SM clock
     alu_peak = 152 * 128 * 2.07e9 / 1e12

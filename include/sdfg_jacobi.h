@@ -15,11 +15,26 @@
  *
  * The boundary ring (row 0, row rows-1, column 0, column cols-1) keeps its
  * input values for ever (Dirichlet).  The result is the full grid after T
- * steps, boundary included.  Every update is evaluated in the order shown,
- * with IEEE round-to-nearest and no fused multiply-add, so FP32 and FP64
- * results do not depend on tiling, on the number of fused steps, or on what
- * else runs in the same batch (BF16 results depend only on the number of fused
- * steps).  FP64 results equal a plain FP64 loop bit for bit.
+ * steps, boundary included; the ring is copied exactly.
+ *
+ * Numerics (IEEE round-to-nearest throughout):
+ *   - FP64: every update is evaluated in the order shown, with no fused
+ *     multiply-add; results equal a plain FP64 loop bit for bit, whatever
+ *     the kernel, tiling, fused depth or batch.
+ *   - FP32 arithmetic (FP32 and BF16 storage): work units that touch the
+ *     boundary ring, the one-step (naive) kernel and the register-resident
+ *     kernel keep the order shown.  Units away from the ring reassociate the
+ *     sum -- they share horizontal pair sums between neighbouring columns,
+ *     carry the unscaled 5-point sums through the k fused steps of a pass and
+ *     multiply by 0.2^k once, at the pass's last step -- which saves about a
+ *     quarter of the FP32 work and is more accurate against FP64, not less.
+ *     FP32 results are therefore bit-identical for the same geometry (fused
+ *     depth k and segment height, hence alone or in any batch or server mix),
+ *     and agree with other geometries to within the FP32 tolerance (max-abs
+ *     1e-4 on fields in [0, 1]) rather than bit for bit.
+ *   - BF16 storage: the steps fused into one pass stay in FP32 registers and
+ *     values are rounded to BF16 each time a pass writes the grid, so the
+ *     result also depends on k.
  *
  * Storage types: FP32 (arithmetic FP32), BF16 (the grid is stored in BF16;
  * arithmetic is FP32, and the steps fused into one pass stay in FP32
@@ -78,18 +93,26 @@ typedef enum {
     SDFG_KERNEL_NAIVE = 1,      /* one timestep per launch, one thread/point */
     SDFG_KERNEL_TEMPORAL = 2,   /* k timesteps per launch (one pass)         */
     SDFG_KERNEL_PERSISTENT = 3, /* one launch for all passes, dependency-driven */
-    SDFG_KERNEL_RESIDENT = 4    /* k timesteps per launch, each CTA's 256 x 112
+    SDFG_KERNEL_RESIDENT = 4,   /* k timesteps per launch, each CTA's 256 x 112
                                    tile held in registers (FP32/BF16 storage;
                                    FP64 runs the temporal kernel instead);
                                    for grids that fit in L2, where a pass is
                                    latency-bound                            */
+    SDFG_KERNEL_SKEWED = 5      /* one launch for all passes; each warp streams
+                                   a chain of seg_rows rows (0 = 1024) of one
+                                   column strip through the k fused steps,
+                                   chains skewed down by k rows per pass so
+                                   that no rows are recomputed between them;
+                                   chunk-level dependencies (tiling in
+                                   (row, time) without halo rows)           */
 } sdfg_kernel;
 
 /*
  * Execution configuration (all fields 0 = choose automatically).
  *   k          timesteps fused per pass: 1, 2, 4 or 8 (paper App. B,
  *              StateFusion/MapToForLoop applied to the timestep loop);
- *   seg_rows   output rows per work unit (MapTiling along rows);
+ *   seg_rows   output rows per work unit (MapTiling along rows); for
+ *              SDFG_KERNEL_SKEWED the chain length;
  *   warps      warps per CTA.
  */
 typedef struct {
@@ -126,11 +149,22 @@ int sdfg_jacobi2d_cfg(const void *in, void *out, int rows, int cols, int ld, int
  *   - rows * cols must not exceed 8,388,608 (SDFG_ERR_INVAL otherwise);
  *   - in/out must be 16-byte aligned and cols a multiple of 4 (ld = cols);
  *   - the first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture;
+ *     that device current); make that first call before any stream capture.
+ *     Under CUDA's lazy module loading (the default) that first look-up also
+ *     loads the library's device code, which reserves the array and may
+ *     synchronise the device; a caller that cannot allow that at an
+ *     arbitrary point makes one call with rows = 0 (or cols = 0) at
+ *     initialisation, which does only this set-up;
  *   - every call shares the one array and it keeps the last call's contents:
  *     calls whose work overlaps on the GPU (other streams, other threads)
  *     race on it, so serialise them.  No element needs to start at zero:
- *     every pass writes each element before it is read.
+ *     every pass writes each element before it is read;
+ *   - it always runs one launch per pass (SDFG_KERNEL_TEMPORAL), with the
+ *     fused depth and segment height the autotuner cached for the shape, or
+ *     the defaults; it never uses the persistent or register-resident
+ *     kernels, so large grids run somewhat slower than sdfg_jacobi2d;
+ *   - a bounded device wait that runs out is recorded in this entry point's
+ *     own error word; sdfg_device_error() reads (and clears) it.
  * Calls no cudaMalloc, cudaFree or other allocating routine.
  */
 int sdfg_jacobi2d_noalloc(const float *in, float *out, int rows, int cols, int T, void *stream);
@@ -151,8 +185,9 @@ int sdfg_jacobi2d_host(const void *h_in, void *h_out, int rows, int cols, int T,
  * with rel_t <= tol, where rel_t = ||A_t - A_{t-1}||_2 / ||A_1 - A_0||_2 over
  * the interior (paper Sec. 3 "State": a transition condition that depends on
  * data).  Squared differences are formed in the storage precision's
- * arithmetic (FP32 for FP32/BF16) and summed in groups of at most 32 terms
- * in FP32; every further level of the reduction is FP64 in a fixed order.
+ * arithmetic (FP32 for FP32/BF16) and summed in groups of at most 48 terms
+ * (one lane: 4 columns x at most 12 rows) in FP32; every further level of
+ * the reduction is FP64 in a fixed order.
  * Outputs: status, steps_done, rel_residual (rel at the final step),
  * r_first2.
  *
@@ -310,7 +345,10 @@ int sdfg_stats_reset(void);
  * recorded events. */
 int sdfg_stats_get(const char *name, long long *launches, double *total_ms);
 
-/* Reads (and with clear != 0 resets) the current device's error word. */
+/* Reads (and with clear != 0 resets) the current device's error words: the
+ * one shared by the allocating entry points and the one of
+ * sdfg_jacobi2d_noalloc.  SDFG_ERR_TIMEOUT if a bounded device wait ran out
+ * since the last clear.  Creates no device state and allocates nothing. */
 int sdfg_device_error(int clear);
 
 /* Thread-local description of the last failure on this thread. */

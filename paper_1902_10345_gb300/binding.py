@@ -22,6 +22,7 @@ SDFG_F32, SDFG_BF16, SDFG_F64 = 0, 1, 2
 SDFG_OK, SDFG_PENDING, SDFG_PAUSED = 0, 1, 2
 SDFG_ERR_INVAL, SDFG_ERR_NOMEM, SDFG_ERR_CUDA, SDFG_ERR_TIMEOUT, SDFG_ERR_BUSY, SDFG_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 SDFG_KERNEL_AUTO, SDFG_KERNEL_NAIVE, SDFG_KERNEL_TEMPORAL, SDFG_KERNEL_PERSISTENT, SDFG_KERNEL_RESIDENT = 0, 1, 2, 3, 4
+SDFG_KERNEL_SKEWED = 5
 
 STATUS_NAMES = {0: "OK", 1: "PENDING", 2: "PAUSED", -1: "ERR_INVAL", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
                 -5: "ERR_BUSY", -6: "ERR_UNSUPPORTED"}

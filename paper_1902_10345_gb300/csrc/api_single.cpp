@@ -38,7 +38,7 @@ int validate_grid(const void *in, const void *out, int R, int C, int ld, long lo
 int resolve_config(const sdfg_config *cfg, int R, int C, int dtype, sdfg_config *out) {
     sdfg_config c = {SDFG_KERNEL_AUTO, 0, 0, 0};
     if (cfg) c = *cfg;
-    if (c.kernel < SDFG_KERNEL_AUTO || c.kernel > SDFG_KERNEL_RESIDENT)
+    if (c.kernel < SDFG_KERNEL_AUTO || c.kernel > SDFG_KERNEL_SKEWED)
         return set_error(SDFG_ERR_INVAL, "unknown kernel family %d", c.kernel);
     if (c.k != 0 && !depth_supported(c.k)) return set_error(SDFG_ERR_INVAL, "k=%d not supported (1, 2, 4, 8)", c.k);
     if (c.seg_rows < 0 || c.warps < 0 || c.warps > MAX_WARPS)
@@ -208,7 +208,9 @@ int run_single(const void *in, void *out, int R, int C, int ld, long long T, int
         if (pc.warps > 4) pc.warps = 4;
         return run_single_persistent(in, out, R, C, ld, T, dtype, pc, st, s);
     }
-    if (c.kernel == SDFG_KERNEL_PERSISTENT) c.kernel = SDFG_KERNEL_TEMPORAL;
+    if (c.kernel == SDFG_KERNEL_SKEWED && tma_ok)
+        return run_single_chain(in, out, R, C, ld, T, dtype, c.k, c.seg_rows, 0, st, s);
+    if (c.kernel == SDFG_KERNEL_PERSISTENT || c.kernel == SDFG_KERNEL_SKEWED) c.kernel = SDFG_KERNEL_TEMPORAL;
 
     if (c.kernel != SDFG_KERNEL_NAIVE && !tma_ok) {
         // stage through two aligned pitched grids

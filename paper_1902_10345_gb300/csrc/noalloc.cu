@@ -69,6 +69,31 @@ int noalloc_setup(NoallocDevice **out) {
 }
 }  // namespace
 
+// The error word of the kernels launched by sdfg_jacobi2d_noalloc on device
+// `dev` (read with cudaMemcpyFromSymbol, reset with cudaMemcpyToSymbol when
+// `clear`): *value = 0 when nothing was recorded, or when the entry point was
+// never set up on that device (then the symbol is not touched, so reading the
+// word never loads this file's module and its static scratch).  Allocates
+// nothing.  Synchronous: waits for the work already on the device.
+int noalloc_error_word(int dev, int clear, int *value) {
+    *value = 0;
+    if (dev < 0 || dev >= 64) return SDFG_OK;
+    bool ready;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        ready = g_dev[dev].ready;
+    }
+    if (!ready) return SDFG_OK;
+    int w = 0;
+    SDFG_CUDA(cudaMemcpyFromSymbol(&w, g_noalloc_err, sizeof(int)));
+    if (clear && w) {
+        const int zero = 0;
+        SDFG_CUDA(cudaMemcpyToSymbol(g_noalloc_err, &zero, sizeof(int)));
+    }
+    *value = w;
+    return SDFG_OK;
+}
+
 }  // namespace sdfg
 
 using namespace sdfg;
@@ -76,7 +101,11 @@ using namespace sdfg;
 extern "C" int sdfg_jacobi2d_noalloc(const float *in, float *out, int rows, int cols, int T, void *stream) {
     if (rows < 0 || cols < 0 || T < 0)
         return set_error(SDFG_ERR_INVAL, "sdfg_jacobi2d_noalloc: rows=%d cols=%d T=%d must be >= 0", rows, cols, T);
-    if (rows == 0 || cols == 0) return SDFG_OK;
+    if (rows == 0 || cols == 0) {
+        // an empty grid does only the per-device set-up (a warm-up call)
+        NoallocDevice *d = nullptr;
+        return noalloc_setup(&d);
+    }
     if (!in || !out) return set_error(SDFG_ERR_INVAL, "sdfg_jacobi2d_noalloc: null grid pointer");
     if (static_cast<size_t>(rows) * static_cast<size_t>(cols) > NOALLOC_MAX_ELEMS)
         return set_error(SDFG_ERR_INVAL,

@@ -202,7 +202,8 @@ struct Rec {
 std::mutex g_stats_mu;
 bool g_stats_on = false;
 std::vector<Rec> g_recs;
-const char *kFamilies[FAM_COUNT] = {"naive", "temporal", "persistent", "reduce", "copy", "stencil3d", "sor", "resident"};
+const char *kFamilies[FAM_COUNT] = {"naive", "temporal", "persistent", "reduce", "copy",
+                                    "stencil3d", "sor", "resident", "skewed"};
 }  // namespace
 
 static thread_local bool g_stats_suspended = false;
@@ -278,13 +279,32 @@ extern "C" int sdfg_stats_get(const char *name, long long *launches, double *tot
     return SDFG_OK;
 }
 
+namespace sdfg {
+int noalloc_error_word(int dev, int clear, int *value);  // noalloc.cu
+}
+
+// Reads the current device's error words: the one of every allocating entry
+// point (only if this device was already set up: a call here creates no
+// device state) and the one of sdfg_jacobi2d_noalloc.
 extern "C" int sdfg_device_error(int clear) {
-    DeviceState *st = nullptr;
-    int rc = current_device(&st);
-    if (rc != SDFG_OK) return rc;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return set_error(SDFG_ERR_UNSUPPORTED, "device index %d out of range", dev);
+    int *word = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_dev_mu);
+        if (g_dev[dev].device >= 0 && g_dev[dev].arch_ok) word = g_dev[dev].d_err;
+    }
     int v = 0;
-    SDFG_CUDA(cudaMemcpy(&v, st->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (clear) SDFG_CUDA(cudaMemset(st->d_err, 0, sizeof(int)));
+    if (word) {
+        SDFG_CUDA(cudaMemcpy(&v, word, sizeof(int), cudaMemcpyDeviceToHost));
+        if (clear && v) SDFG_CUDA(cudaMemset(word, 0, sizeof(int)));
+    }
+    int w = 0;
+    const int rc = noalloc_error_word(dev, clear, &w);
+    if (rc != SDFG_OK) return rc;
+    if (!v) v = w;
     if (v == DEV_ERR_TIMEOUT_TMA || v == DEV_ERR_TIMEOUT_DEP) return SDFG_ERR_TIMEOUT;
     return v == 0 ? SDFG_OK : SDFG_ERR_CUDA;
 }

@@ -85,6 +85,7 @@ enum Family {
     FAM_STENCIL3D,
     FAM_SOR,
     FAM_RESIDENT,
+    FAM_SKEWED,
     FAM_COUNT
 };
 TimedLaunch stats_begin(int family, cudaStream_t s);
@@ -112,5 +113,12 @@ std::vector<int> plan_resident_passes(long long T, int k);
 // and `second`; *final receives the buffer holding the result.
 int run_resident_passes(const void *src0, void *first, void *second, const std::vector<int> &ks, int R, int C,
                         int ld, int dtype, DeviceState *st, cudaStream_t s, void **final);
+
+// ---- skewed chains (skewed.cu) ------------------------------------------------
+// T steps of one grid in one launch of the chain kernel: passes of depth k,
+// chains of L rows (0: 1024), progress published every `pub` chunks (0: 4).
+// in/out must be TMA-compatible; in == out allowed.
+int run_single_chain(const void *in, void *out, int R, int C, int ld, long long T, int dtype, int k, int L, int pub,
+                     DeviceState *st, cudaStream_t s);
 
 }  // namespace sdfg

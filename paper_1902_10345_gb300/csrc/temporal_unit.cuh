@@ -147,6 +147,58 @@ __host__ __device__ constexpr double pow_fifth(int k) { return k <= 0 ? 1.0 : 0.
 // 5^k (exact in FP32 for k <= 10).
 __host__ __device__ constexpr float pow_five(int k) { return k <= 0 ? 1.0f : 5.0f * pow_five(k - 1); }
 
+// The reassociated level with a two-row register ring.  Level l keeps, for the
+// row c it received last, that row itself (`a`) and its output's partial sum
+// north + (w + c + e) (`p`); the output of row c is complete as soon as its
+// south row x arrives:
+//     o(c)   = p(c) + x            (one add on the level-to-level path)
+//     p(x)   = a(c) + H3(x)        (H3: the horizontal three-point sum of x)
+//     a      <- x
+// H3 shares the pair sums q = u0 + u1 and u2 + u3 between neighbouring columns
+// (h0 = w + q01, h1 = q01 + u2, h2 = u1 + q23, h3 = q23 + e).  The sum is
+// carried unscaled (level l holds 5^l times the state), as in level_sum.
+// PAIRS_SPLIT: x, a, p and o pack the column pairs (0, 2), (1, 3);
+// PAIRS_ENTRY: x, a and p are pairs (0, 1), (2, 3) as a 16-byte load leaves a
+// row, and o is formed by scalar adds (the next level packs it split).
+template <int V, int PAIRS>
+__device__ __forceinline__ void level_p(float (&o)[V], float (&a)[V], float (&p)[V], const float (&x)[V]) {
+    static_assert(V == 4, "the two-row ring packs four columns per lane");
+    const float left = __shfl_up_sync(FULL_MASK, x[V - 1], 1);
+    const float right = __shfl_down_sync(FULL_MASK, x[0], 1);
+    if constexpr (PAIRS == PAIRS_SPLIT) {
+        const float2 o02 = __fadd2_rn(make_float2(p[0], p[2]), make_float2(x[0], x[2]));
+        const float2 o13 = __fadd2_rn(make_float2(p[1], p[3]), make_float2(x[1], x[3]));
+        o[0] = o02.x;
+        o[2] = o02.y;
+        o[1] = o13.x;
+        o[3] = o13.y;
+        const float2 q = __fadd2_rn(make_float2(x[0], x[2]), make_float2(x[1], x[3]));
+        const float2 h02 = make_float2(__fadd_rn(left, q.x), __fadd_rn(x[1], q.y));
+        const float2 h13 = make_float2(__fadd_rn(q.x, x[2]), __fadd_rn(q.y, right));
+        const float2 p02 = __fadd2_rn(make_float2(a[0], a[2]), h02);
+        const float2 p13 = __fadd2_rn(make_float2(a[1], a[3]), h13);
+        p[0] = p02.x;
+        p[2] = p02.y;
+        p[1] = p13.x;
+        p[3] = p13.y;
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) o[e] = __fadd_rn(p[e], x[e]);
+        const float q01 = __fadd_rn(x[0], x[1]);
+        const float q23 = __fadd_rn(x[2], x[3]);
+        const float2 h01 = make_float2(__fadd_rn(left, q01), __fadd_rn(q01, x[2]));
+        const float2 h23 = make_float2(__fadd_rn(x[1], q23), __fadd_rn(q23, right));
+        const float2 p01 = __fadd2_rn(make_float2(a[0], a[1]), h01);
+        const float2 p23 = __fadd2_rn(make_float2(a[2], a[3]), h23);
+        p[0] = p01.x;
+        p[1] = p01.y;
+        p[2] = p23.x;
+        p[3] = p23.y;
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) a[e] = x[e];
+}
+
 template <int V, bool COLCHK>
 __device__ __forceinline__ void level_row(double (&o)[V], const double (&n)[V], const double (&c)[V],
                                           const double (&s)[V], unsigned colmask) {
@@ -190,6 +242,25 @@ __device__ __noinline__ inline bool drain_after_timeout(uint64_t *bars, uint32_t
 #ifndef SDFG_SPLIT_PAIRS
 #define SDFG_SPLIT_PAIRS 1
 #endif
+#ifndef SDFG_RING2
+#define SDFG_RING2 1  // reassociated units keep two rows per level (level_p)
+#endif
+#ifndef SDFG_RING2_TURN
+#define SDFG_RING2_TURN 4  // rows per turn of the two-row-ring chunk loop
+#endif
+static_assert(CHUNK_ROWS % SDFG_RING2_TURN == 0, "chunks are whole turns");
+
+// Hook of UnitPipe::run for work units that depend on other units while they
+// stream (the chain kernel, skewed.cu).  The whole warp calls ready(c) before
+// chunk c is loaded (false: a bounded wait ran out) and done(c) once chunk c's
+// rows are stored and the warp is synchronised.  EDGES: a unit of the
+// reassociated pipe may hold row 0 or row R-1 (see step2).  The units of the
+// per-pass and persistent kernels need none of it.
+struct NoHook {
+    static constexpr bool EDGES = false;
+    __device__ __forceinline__ bool ready(int) { return true; }
+    __device__ __forceinline__ void done(int) {}
+};
 
 template <class ST, int V, int K, bool COLCHK, bool RES, bool EXACT>
 struct UnitPipe {
@@ -202,13 +273,21 @@ struct UnitPipe {
     static constexpr int PAIRS1 = SPLIT ? PAIRS_SPLIT : PAIRS_NATURAL;
     static constexpr int W = 32 * V;
     static constexpr uint32_t CHUNK_BYTES = CHUNK_ROWS * W * sizeof(ST);
+    // units away from the boundary ring reassociate (see level_sum); a unit
+    // that holds a boundary row or column keeps the exact order throughout
+    static constexpr bool SCALED = sizeof(CT) == 4 && !EXACT;
+    // reassociated units with four columns per lane use the two-row ring
+    static constexpr bool RING2 = SCALED && SDFG_RING2 && V == 4;
 
     CT b[K][3][V];  // level l, ring slot, column: rows r-l-2, r-l-1, r-l of level l
+    CT ra[K][V];    // two-row ring (RING2): level l's last row ...
+    CT rp[K][V];    // ... and its output's partial sum (see level_p)
 
     const void *tmap;
     ST *dst;
     int ld, R, C;
     int X, y0, y1, rb, n_steps, n_chunks;
+    int sy0, sy1;  // rows the reassociated pipe stores: [y0, y1) without the boundary rows
     uint32_t base;
     ST *ring;
     uint64_t *bars;
@@ -261,9 +340,6 @@ struct UnitPipe {
         constexpr int SN = (PH + 1) % 3;  // slot of the north row
         constexpr int SC = (PH + 2) % 3;  // slot of the centre row
         constexpr int SS = PH;            // slot of the south (newest) row
-        // units away from the boundary ring reassociate (see level_sum); a unit
-        // that holds a boundary row or column keeps the exact order throughout
-        constexpr bool SCALED = sizeof(CT) == 4 && !EXACT;
         {
             CT tmp[V];
             VecIO<ST, V>::load(tmp, src);
@@ -336,6 +412,99 @@ struct UnitPipe {
         }
     }
 
+    // The pass's scale factor 0.2^K on the last level's output, split hi + lo
+    // so the product is rounded once from a ~48-bit factor.
+    template <int PAIRS_LAST>
+    __device__ __forceinline__ static void scale_last(CT (&o)[V]) {
+        constexpr double F = pow_fifth(K);
+        constexpr float FHI = static_cast<float>(F);
+        constexpr float FLO = static_cast<float>(F - static_cast<double>(FHI));
+        constexpr bool SP = PAIRS_LAST != PAIRS_NATURAL;  // the column pairs the level packs
+        constexpr int STEP = SP ? V / 2 : 1;
+#pragma unroll
+        for (int p = 0; p < V / 2; ++p) {
+            const int e0 = SP ? p : 2 * p;
+            const float2 u = make_float2(o[e0], o[e0 + STEP]);
+            const float2 t = __fmul2_rn(u, make_float2(FLO, FLO));
+            const float2 f = __ffma2_rn(u, make_float2(FHI, FHI), t);
+            o[e0] = f.x;
+            o[e0 + STEP] = f.y;
+        }
+    }
+
+    // One input row r through all K levels of the two-row ring (RING2).
+    // Level l's output at this row is centre row r-l-1, as in `step`.
+    // EDGE: row 0 or row R-1 may be a centre row.  A boundary row keeps its
+    // value, which a level holds scaled like every other row (5^l times the
+    // state, each factor 5 rounded once), so its neighbours' sums stay
+    // consistent; such rows are never stored by this pipe (sy0 >= 1,
+    // sy1 <= R-1): the caller provides them in the destination grid.
+    template <bool EDGE>
+    __device__ __forceinline__ void step2(int r, const ST *src, ST *out) {
+        CT x[V];
+        VecIO<ST, V>::load(x, src);
+#pragma unroll
+        for (int l = 0; l < K; ++l) {
+            CT o[V];
+            CT cen[V];  // the centre row (for the residual sums and the boundary)
+            if (RES || EDGE) {
+#pragma unroll
+                for (int e = 0; e < V; ++e) cen[e] = ra[l][e];
+            }
+            if (l == 0)
+                level_p<V, PAIRS0>(o, ra[l], rp[l], x);
+            else
+                level_p<V, PAIRS_SPLIT>(o, ra[l], rp[l], x);
+            if (EDGE) {
+                const int rc = r - l - 1;
+                if (rc == 0 || rc == R - 1) {
+#pragma unroll
+                    for (int e = 0; e < V; ++e) o[e] = __fmul_rn(5.0f, cen[e]);
+                }
+            }
+            if (l == K - 1) scale_last<(K == 1 ? PAIRS0 : PAIRS_SPLIT)>(o);
+            if (RES && l == 0 && (res_flags & 1)) {
+                const int row = r - 1;
+                if (row >= y0 && row < y1 && row >= 1 && row <= R - 2) {
+                    CT a1[V];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) a1[e] = K > 1 ? CT(0.2f) * o[e] : o[e];
+                    accumulate(g_ref, a1, cen);
+                }
+            }
+            if (l == K - 1) {
+                const int row = r - K;
+                if (row >= sy0 && row < sy1) {
+                    if (RES && (res_flags & 2) && row >= 1 && row <= R - 2) {
+                        CT prev[V];
+                        constexpr CT PS = CT(pow_fifth(K - 1));
+#pragma unroll
+                        for (int e = 0; e < V; ++e) prev[e] = PS * cen[e];
+                        accumulate(g_chk, o, prev);
+                    }
+                    store_row(out, o);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) x[e] = o[e];
+            }
+        }
+    }
+
+    template <bool EDGE>
+    __device__ __forceinline__ void chunk_body2(int r0, const ST *src, ST *out) {
+        constexpr int TURN = SDFG_RING2_TURN;
+        const size_t ldr = static_cast<size_t>(ld);
+#pragma unroll 1
+        for (int h = 0; h < CHUNK_ROWS / TURN; ++h) {
+#pragma unroll
+            for (int i = 0; i < TURN; ++i) step2<EDGE>(r0 + i, src + i * W, out + i * ldr);
+            r0 += TURN;
+            src += TURN * W;
+            out += TURN * ldr;
+        }
+    }
+
     // `out` points at output row r0-K (it is only dereferenced for rows the
     // unit owns).  The chunk is CHUNK_ROWS/3 turns of one 3-row body: a
     // small hot loop (instruction cache).
@@ -354,19 +523,37 @@ struct UnitPipe {
     }
 
     __device__ __forceinline__ bool run() {
+        NoHook hk;
+        return run(hk);
+    }
+
+    template <class Hook>
+    __device__ __forceinline__ bool run(Hook &hk) {
+        if constexpr (RING2) {
 #pragma unroll
-        for (int l = 0; l < K; ++l)
+            for (int l = 0; l < K; ++l)
 #pragma unroll
-            for (int s = 0; s < 3; ++s)
+                for (int e = 0; e < V; ++e) ra[l][e] = rp[l][e] = CT(0);
+        } else {
 #pragma unroll
-                for (int e = 0; e < V; ++e) b[l][s][e] = CT(0);
+            for (int l = 0; l < K; ++l)
+#pragma unroll
+                for (int s = 0; s < 3; ++s)
+#pragma unroll
+                    for (int e = 0; e < V; ++e) b[l][s][e] = CT(0);
+        }
         if (RES) {
             g_ref = g_chk = CT(0);
             acc_ref = acc_chk = 0.0;
         }
-        if (lane == 0) {
+        int issued = 0;  // chunks whose load was issued
+        {
             const int first = n_chunks < STAGES ? n_chunks : STAGES;
-            for (int c = 0; c < first; ++c) issue(c);
+            for (int c = 0; c < first; ++c) {
+                if (!hk.ready(c)) return drain_after_timeout(bars, base, issued, 0);
+                if (lane == 0) issue(c);
+                ++issued;
+            }
         }
         for (int c = 0; c < n_chunks; ++c) {
             const uint32_t g = base + static_cast<uint32_t>(c);
@@ -374,7 +561,7 @@ struct UnitPipe {
             // every lane waits (acquiring the TMA-written rows); the outcome is
             // made warp-uniform so no lane is left behind in a shuffle
             const bool ok = mbar_wait_bounded(&bars[slot], (g / STAGES) & 1u, timeout_ns);
-            if (!__all_sync(FULL_MASK, ok)) return drain_after_timeout(bars, base, n_chunks, c);
+            if (!__all_sync(FULL_MASK, ok)) return drain_after_timeout(bars, base, issued, c);
             const int r0 = rb + c * CHUNK_ROWS;
             const ST *src = ring + slot * (CHUNK_ROWS * W) + lane * V;
             // Rows past the unit's last step are in the box (zero-filled past
@@ -388,13 +575,26 @@ struct UnitPipe {
             // code small (instruction cache).  Exact-order units keep both:
             // their checked body tests every level's row.
             constexpr bool ONE_BODY = SDFG_SCALED_ONE_BODY && sizeof(CT) == 4 && !EXACT;
-            if (fast && !ONE_BODY)
+            if constexpr (RING2) {
+                // a centre row of some level may be row 0 or row R-1
+                const bool edge = Hook::EDGES && (r0 <= K || (r0 + CHUNK_ROWS - 2 >= R - 1 && r0 - K <= R - 1));
+                if (edge)
+                    chunk_body2<true>(r0, src, out);
+                else
+                    chunk_body2<false>(r0, src, out);
+            } else if (fast && !ONE_BODY) {
                 chunk_body<false>(r0, src, out);
-            else
+            } else {
                 chunk_body<true>(r0, src, out);
-            // every lane has consumed chunk c: recycle its slot
+            }
+            // every lane has consumed chunk c (and stored its rows): recycle its slot
             __syncwarp();
-            if (lane == 0 && c + STAGES < n_chunks) issue(c + STAGES);
+            hk.done(c);
+            if (c + STAGES < n_chunks) {
+                if (!hk.ready(c + STAGES)) return drain_after_timeout(bars, base, issued, c + 1);
+                if (lane == 0) issue(c + STAGES);
+                ++issued;
+            }
             if (RES) {
                 acc_ref += static_cast<double>(g_ref);
                 acc_chk += static_cast<double>(g_chk);
@@ -444,6 +644,7 @@ __device__ __forceinline__ bool run_unit(const void *tmap, ST *dst, const GridGe
         UnitPipe<ST, V, K, CHK, RS, EX> p;                                                                  \
         p.tmap = tmap; p.dst = dst; p.ld = g.ld; p.R = g.R; p.C = g.C;                                  \
         p.X = X; p.y0 = y0; p.y1 = y1; p.rb = rb; p.n_steps = n_steps; p.n_chunks = n_chunks;           \
+        p.sy0 = y0; p.sy1 = y1;                                                                         \
         p.base = chunk_ctr; p.ring = ring; p.bars = bars; p.lane = lane;                                \
         p.colmask = colmask; p.resmask = resmask; p.own_lane = own_lane; p.full_vec = full_vec;         \
         p.res_flags = res_flags; p.timeout_ns = timeout_ns;                                             \

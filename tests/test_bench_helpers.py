@@ -67,8 +67,8 @@ def test_median_ci95():
 
 def test_kernel_names():
     class B:
-        SDFG_KERNEL_TEMPORAL, SDFG_KERNEL_PERSISTENT, SDFG_KERNEL_RESIDENT = 2, 3, 4
+        SDFG_KERNEL_TEMPORAL, SDFG_KERNEL_PERSISTENT, SDFG_KERNEL_RESIDENT, SDFG_KERNEL_SKEWED = 2, 3, 4, 5
 
-    assert [bench.kernel_code(B, n) for n in ("temporal", "persistent", "resident")] == [2, 3, 4]
+    assert [bench.kernel_code(B, n) for n in ("temporal", "persistent", "resident", "skewed")] == [2, 3, 4, 5]
     with pytest.raises(KeyError):
         bench.kernel_code(B, "naive")

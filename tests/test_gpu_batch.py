@@ -156,9 +156,10 @@ def test_solve_random_matches_oracle():
 
 
 def test_solve_bf16_invariants():
-    """BF16 storage rounds every step, so on a Laplace solve with boundary
-    values near +-1 (ulp 2^-7) updates below half an ulp stall and the state
-    drifts from the FP64 trajectory; the FP64-oracle tolerance does not apply.
+    """BF16 storage rounds the grid each time a pass stores it (every k
+    steps), so on a Laplace solve with boundary values near +-1 (ulp 2^-7)
+    increments below half an ulp per pass stall and the state drifts from the
+    FP64 trajectory; the FP64-oracle tolerance does not apply.
     What must hold: the stop rule (rel <= tol at a check step, or the cap),
     the discrete maximum principle up to one BF16 ulp, an untouched boundary,
     and the same result alone as in a batch."""
@@ -247,8 +248,7 @@ def test_full_512_grid_batch_in_the_bench_configuration():
     in [64, 2048], T in [50, 500], each grid pitched to 16-byte rows) in the
     configuration it measures (one persistent launch, k = 4, 256-row
     segments, replayed from a plan): every grid runs exactly T steps, and
-    sampled grids across the size range match the FP64 oracle -- small ones
-    whole, large ones on light-cone windows."""
+    every one of the 512 results matches the FP64 oracle on every element."""
     import ctypes
     specs = inputs.batch_specs(512, seed=0)
     xs, ys, descs = [], [], []
@@ -274,20 +274,8 @@ def test_full_512_grid_batch_in_the_bench_configuration():
     assert binding.sdfg_device_error(True) == 0
     for d, sp in zip(arr, specs):
         assert d.status == 0 and d.steps_done == sp.T
-    # samples: the smallest, the largest and a spread in between
-    order = sorted(range(len(specs)), key=lambda g: specs[g].rows * specs[g].cols)
-    picks = [order[0], order[1], order[len(order) // 4], order[len(order) // 2], order[3 * len(order) // 4],
-             order[-2], order[-1]]
-    for g in picks:
-        sp, x, y = specs[g], xs[g], ys[g]
-        xh = h64(x)
-        if sp.rows * sp.cols <= 300_000:
-            want = oracle.jacobi2d(xh, sp.T, threads=0)
-            assert np.abs(h64(y) - want).max() <= TOL[F32], (g, sp)
-        else:
-            R, C = sp.rows, sp.cols
-            for (r0, c0) in [(0, 0), (R // 2, C // 2), (R - 6, C - 6), (R // 3, C - 6)]:
-                r0, c0 = max(0, min(r0, R - 6)), max(0, min(c0, C - 6))
-                want = oracle.jacobi2d_window(xh, sp.T, r0, r0 + 6, c0, c0 + 6, threads=0)
-                got = h64(y[r0:r0 + 6, c0:c0 + 6])
-                assert np.abs(got - want).max() <= TOL[F32], (g, sp, r0, c0)
+    # every grid whole against the oracle (all host threads)
+    for g, (sp, x, y) in enumerate(zip(specs, xs, ys)):
+        want = oracle.jacobi2d(h64(x), sp.T, threads=0)
+        err = np.abs(h64(y) - want).max()
+        assert err <= TOL[F32], (g, sp, err)

@@ -68,8 +68,13 @@ def cfg(kernel, k=0, seg_rows=0, warps=0):
 
 
 PERSISTENT = binding.SDFG_KERNEL_PERSISTENT
+SKEWED = binding.SDFG_KERNEL_SKEWED
+# the chain kernel at several depths and chain lengths (short chains put many
+# chain seams, and tiny first/last chains, into small grids)
+SKEWED_CFGS = [cfg(SKEWED, 8), cfg(SKEWED, 8, seg_rows=32), cfg(SKEWED, 4, seg_rows=24), cfg(SKEWED, 2, seg_rows=8),
+               cfg(SKEWED, 1, seg_rows=4)]
 ALL_CFGS = [cfg(NAIVE)] + [cfg(TEMPORAL, k) for k in (1, 2, 4, 8)] + [cfg(TEMPORAL, 8, seg_rows=16, warps=4),
-                                                                     cfg(TEMPORAL, 4, seg_rows=24, warps=2)]
+                                                                     cfg(TEMPORAL, 4, seg_rows=24, warps=2)] + SKEWED_CFGS
 # (per-pass, persistent) pairs with the same geometry: bit-identical results
 SAME_GEOMETRY = [(cfg(TEMPORAL, 8, seg_rows=24, warps=4), cfg(PERSISTENT, 8, seg_rows=24, warps=4)),
                  (cfg(TEMPORAL, 4, seg_rows=48, warps=2), cfg(PERSISTENT, 4, seg_rows=48, warps=4))]
@@ -103,7 +108,7 @@ def test_other_dtypes_match_oracle(dt, shape, T):
     x = dev(g, dt)
     want = oracle.jacobi2d(host64(x), T, threads=0)
     outs = []
-    for c in [cfg(NAIVE), cfg(TEMPORAL, 1), cfg(TEMPORAL, 2), cfg(TEMPORAL, 4), cfg(TEMPORAL, 8)]:
+    for c in [cfg(NAIVE), cfg(TEMPORAL, 1), cfg(TEMPORAL, 2), cfg(TEMPORAL, 4), cfg(TEMPORAL, 8)] + SKEWED_CFGS:
         y = host64(run(x, T, c))
         err = np.abs(y - want).max()
         assert err <= TOL[dt], (dt, shape, T, c.k, err)
@@ -139,7 +144,7 @@ def test_f32_256_grid_T100():
 def test_in_place(T):
     g = inputs.uniform_grid(70, 90, seed=T)
     want = oracle.jacobi2d(g.astype(np.float32).astype(np.float64), T)
-    for c in [cfg(TEMPORAL, 8), cfg(TEMPORAL, 4), cfg(NAIVE)]:
+    for c in [cfg(TEMPORAL, 8), cfg(TEMPORAL, 4), cfg(NAIVE), cfg(SKEWED, 8, seg_rows=32), cfg(SKEWED, 4, seg_rows=16)]:
         x = dev(g, F32)
         run(x, T, c, inplace=True)
         assert np.abs(host64(x) - want).max() <= TOL[F32]
@@ -152,10 +157,11 @@ def test_pitched_and_unaligned_layouts(ld_extra):
     R, C, T = 50, 68, 13
     g = inputs.uniform_grid(R, C, seed=ld_extra)
     x = dev(g, F32, ld=C + ld_extra)
-    y = dev(np.zeros((R, C)), F32, ld=C + ld_extra)
-    run(x, T, cfg(TEMPORAL, 4), out=y)
     want = oracle.jacobi2d(host64(x), T)
-    assert np.abs(host64(y) - want).max() <= TOL[F32]
+    for c in [cfg(TEMPORAL, 4), cfg(SKEWED, 4, seg_rows=16)]:
+        y = dev(np.zeros((R, C)), F32, ld=C + ld_extra)
+        run(x, T, c, out=y)
+        assert np.abs(host64(y) - want).max() <= TOL[F32], c.kernel
 
 
 @pytest.mark.parametrize("cols", [61, 127, 129, 8190 // 64])
@@ -164,7 +170,7 @@ def test_ragged_widths(cols):
     g = inputs.uniform_grid(R, cols, seed=cols)
     x = dev(g, F32)
     want = oracle.jacobi2d(host64(x), T)
-    for c in [cfg(TEMPORAL, 8), cfg(TEMPORAL, 2)]:
+    for c in [cfg(TEMPORAL, 8), cfg(TEMPORAL, 2), cfg(SKEWED, 8, seg_rows=32)]:
         assert np.abs(host64(run(x, T, c)) - want).max() <= TOL[F32]
 
 
@@ -226,6 +232,81 @@ def test_full_size_8192_T1000_windows_and_properties():
     # boundary ring untouched
     assert torch.equal(y[0], x[0]) and torch.equal(y[-1], x[-1])
     assert torch.equal(y[:, 0], x[:, 0]) and torch.equal(y[:, -1], x[:, -1])
+
+
+def test_full_size_8192_T1000_whole_grid():
+    """The bench workload in the bench's launch configuration (persistent
+    kernel, k = 8, 128-row segments, 4 warps per CTA), compared with the FP64
+    oracle on EVERY element: every unit seam of the reassociated interior
+    units, the edge units and the boundary ring.  The oracle runs the whole
+    grid on all host threads."""
+    R = C = 8192
+    T = 1000
+    g = inputs.uniform_grid(R, C, seed=0)
+    x = dev(g, F32)
+    bench_cfg = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=8, seg_rows=128, warps=4)
+    y = host64(run(x, T, bench_cfg))
+    want = oracle.jacobi2d(host64(x), T, threads=0)
+    err = np.abs(y - want)
+    assert err.max() <= TOL[F32], (float(err.max()), np.unravel_index(int(err.argmax()), err.shape))
+
+
+@pytest.mark.parametrize("shape", [(520, 520), (530, 700), (400, 1130)])
+@pytest.mark.parametrize("T", [8, 37, 64])
+def test_bench_geometry_multi_seam_whole(shape, T):
+    """The bench's geometry (k = 8, 128-row segments) on grids of at least
+    three segments and three strips, so that reassociated interior units and
+    all their seams (128-row and 112-column) are compared whole with the
+    oracle, for the streamed and the persistent kernel; T = 37 adds the
+    remainder passes (4 + 1 steps).  The two kernels run the same units and
+    must agree bit for bit."""
+    R, C = shape
+    g = inputs.uniform_grid(R, C, seed=R + 7 * C + T)
+    x = dev(g, F32)
+    want = oracle.jacobi2d(host64(x), T, threads=0)
+    outs = []
+    for kern in (TEMPORAL, PERSISTENT):
+        y = host64(run(x, T, cfg(kern, 8, seg_rows=128, warps=4)))
+        err = np.abs(y - want).max()
+        assert err <= TOL[F32], (shape, T, kern, err)
+        outs.append(y)
+    assert np.array_equal(outs[0], outs[1]), "same geometry, different bits"
+    info = binding.sdfg_plan_geometry(R, C, F32, 8, 128)
+    assert info["n_strips"] >= 3 and info["n_segs"] >= 3, info
+
+
+@pytest.mark.parametrize("shape,L", [((2100, 700), 1024), ((1300, 1130), 256), ((777, 333), 100)])
+@pytest.mark.parametrize("T", [8, 37, 96])
+def test_skewed_chains_whole(shape, L, T):
+    """The chain kernel (chains of L rows skewed down by k rows per pass,
+    chunk-level dependencies): several chains and strips, compared whole
+    with the oracle; T = 37 adds remainder passes (8 x 4 + 4 + 1), whose
+    depths change from pass to pass; the boundary ring comes out exact; and
+    a repeat call (cached plan, counters reset) gives the same bits."""
+    R, C = shape
+    g = inputs.uniform_grid(R, C, seed=R + C + T)
+    x = dev(g, F32)
+    want = oracle.jacobi2d(host64(x), T, threads=0)
+    c = cfg(SKEWED, 8, seg_rows=L)
+    y1 = run(x, T, c)
+    err = np.abs(host64(y1) - want).max()
+    assert err <= TOL[F32], (shape, L, T, err)
+    assert torch.equal(y1[0], x[0]) and torch.equal(y1[-1], x[-1])
+    assert torch.equal(y1[:, 0], x[:, 0]) and torch.equal(y1[:, -1], x[:, -1])
+    y2 = run(x, T, c)
+    assert torch.equal(y1, y2)
+
+
+def test_skewed_full_size_8192_T1000_whole_grid():
+    """The chain kernel on the bench workload, k = 8, chains of 1024 rows,
+    against the FP64 oracle on every element."""
+    R = C = 8192
+    T = 1000
+    x = dev(inputs.uniform_grid(R, C, seed=0), F32)
+    y = host64(run(x, T, cfg(SKEWED, 8, seg_rows=1024)))
+    want = oracle.jacobi2d(host64(x), T, threads=0)
+    err = np.abs(y - want)
+    assert err.max() <= TOL[F32], (float(err.max()), np.unravel_index(int(err.argmax()), err.shape))
 
 
 def test_paper_workload_eigenmode_2048_T1024():

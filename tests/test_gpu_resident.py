@@ -130,7 +130,7 @@ def test_paper_workload_eigenmode_2048_T1024():
 def test_unknown_kernel_family_and_depth_rejected():
     x = torch.rand((40, 50), device="cuda")
     y = torch.empty_like(x)
-    for bad in (binding.config(kernel=RESIDENT + 1), binding.config(kernel=-1), binding.config(kernel=RESIDENT, k=3),
+    for bad in (binding.config(kernel=binding.SDFG_KERNEL_SKEWED + 1), binding.config(kernel=-1), binding.config(kernel=RESIDENT, k=3),
                 binding.config(kernel=RESIDENT, k=16)):
         rc = binding.sdfg_jacobi2d_cfg(x.data_ptr(), y.data_ptr(), 40, 50, 50, 5, F32, bad, 0)
         assert rc == binding.SDFG_ERR_INVAL, (bad.kernel, bad.k, rc)
