@@ -99,7 +99,7 @@ typedef enum {
                                    for grids that fit in L2, where a pass is
                                    latency-bound                            */
     SDFG_KERNEL_SKEWED = 5      /* one launch for all passes; each warp streams
-                                   a chain of seg_rows rows (0 = 1024) of one
+                                   a chain of seg_rows rows (0 = 512) of one
                                    column strip through the k fused steps,
                                    chains skewed down by k rows per pass so
                                    that no rows are recomputed between them;
@@ -341,8 +341,9 @@ int sdfg_autotune_batch(const sdfg_desc *desc, int n, int check_stride, sdfg_con
 int sdfg_stats_enable(int on);
 int sdfg_stats_reset(void);
 /* Sums over launches of kernel family `name` ("naive", "temporal",
- * "persistent", "reduce", "copy", "stencil3d", "sor"); waits for the
- * recorded events. */
+ * "persistent", "reduce", "copy", "stencil3d", "sor", "resident",
+ * "skewed"), or over the host copies of sdfg_jacobi2d_host ("h2d",
+ * "d2h"); waits for the recorded events. */
 int sdfg_stats_get(const char *name, long long *launches, double *total_ms);
 
 /* Reads (and with clear != 0 resets) the current device's error words: the

@@ -45,11 +45,15 @@ int resolve_config(const sdfg_config *cfg, int R, int C, int dtype, sdfg_config 
         return set_error(SDFG_ERR_INVAL, "bad seg_rows/warps (%d/%d)", c.seg_rows, c.warps);
     sdfg_config tuned;
     const bool have = autotune_lookup(R, C, dtype, &tuned);
-    // large grids: one persistent launch for all passes (no per-pass tail);
-    // small grids: one launch per pass
-    if (c.kernel == SDFG_KERNEL_AUTO)
-        c.kernel = have ? tuned.kernel
-                        : (static_cast<long long>(R) * C >= (1LL << 20) ? SDFG_KERNEL_PERSISTENT : SDFG_KERNEL_TEMPORAL);
+    // large grids: one launch for all passes (no per-pass tail) -- the chain
+    // kernel for FP32/BF16 storage, the persistent kernel for FP64; small
+    // grids: one launch per pass
+    if (c.kernel == SDFG_KERNEL_AUTO) {
+        const bool large = static_cast<long long>(R) * C >= (1LL << 20);
+        c.kernel = have    ? tuned.kernel
+                   : large ? (dtype == SDFG_F64 ? SDFG_KERNEL_PERSISTENT : SDFG_KERNEL_SKEWED)
+                           : SDFG_KERNEL_TEMPORAL;
+    }
     if (c.k == 0) c.k = have && tuned.k ? tuned.k : default_depth(dtype);
     if (c.warps == 0) c.warps = have && tuned.warps ? tuned.warps : 4;
     if (c.seg_rows == 0 && have) c.seg_rows = tuned.seg_rows;
@@ -331,10 +335,16 @@ extern "C" int sdfg_jacobi2d_host(const void *h_in, void *h_out, int rows, int c
         g_host_cache.bytes = bytes;
         g_host_cache.device = st->device;
     }
-    SDFG_CUDA(cudaMemcpyAsync(g_host_cache.a, h_in, bytes, cudaMemcpyHostToDevice, s));
+    TimedLaunch t_in = stats_begin(FAM_H2D, s);
+    cudaError_t e = cudaMemcpyAsync(g_host_cache.a, h_in, bytes, cudaMemcpyHostToDevice, s);
+    stats_end(t_in, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync (host to device)");
     rc = run_single(g_host_cache.a, g_host_cache.b, rows, cols, cols, T, dtype, nullptr, true, s);
     if (rc != SDFG_OK) return rc;
-    SDFG_CUDA(cudaMemcpyAsync(h_out, g_host_cache.b, bytes, cudaMemcpyDeviceToHost, s));
+    TimedLaunch t_out = stats_begin(FAM_D2H, s);
+    e = cudaMemcpyAsync(h_out, g_host_cache.b, bytes, cudaMemcpyDeviceToHost, s);
+    stats_end(t_out, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync (device to host)");
     SDFG_CUDA(cudaStreamSynchronize(s));
     return SDFG_OK;
 }

@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "runtime.h"
 
@@ -104,59 +105,41 @@ extern "C" int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *
     cudaEventCreate(&e1);
     // probe length: enough steps that each candidate runs a few passes
     const long long Tp = std::min<long long>(T, 64);
-    const int ks[] = {2, 4, 8};
-    const int kernels[] = {SDFG_KERNEL_TEMPORAL, SDFG_KERNEL_PERSISTENT};
     // short segments give small grids enough units to fill the GPU; tall ones
-    // cut the halo rows of large grids
+    // cut the halo rows of large grids; the chain kernel takes chain lengths
     const int segs_c[] = {24, 48, 96, 128, 192};
-    float best_ms = 1e30f;
-    sdfg_config winner = {SDFG_KERNEL_TEMPORAL, default_depth(dtype), 0, 4};
+    const int chains_c[] = {256, 512, 1024};
+    std::vector<sdfg_config> cands;
     // the register-resident pass is a candidate where both grids fit in L2
     // (there a pass is latency-bound, which is what it shortens)
     const bool try_resident = resident_supported(dtype) && 2 * bytes <= (96ull << 20);
-    for (int k : ks) {
-        for (int kern : kernels) {
-            for (int sr : segs_c) {
-                if (sr > rows) continue;
-                sdfg_config c = {kern, k, sr, 4};
-                // warm-up, then timed
-                rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);
-                if (rc != SDFG_OK) break;
-                cudaEventRecord(e0, s);
-                rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);
-                cudaEventRecord(e1, s);
-                if (rc != SDFG_OK) break;
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    rc = cuda_error(cudaGetLastError(), "autotune sync");
-                    break;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    winner = c;
-                }
-            }
-            if (rc != SDFG_OK) break;
-        }
+    for (int k : {2, 4, 8}) {
+        for (int kern : {SDFG_KERNEL_TEMPORAL, SDFG_KERNEL_PERSISTENT})
+            for (int sr : segs_c)
+                if (sr <= rows) cands.push_back(sdfg_config{kern, k, sr, 4});
+        for (int L : chains_c)
+            if (L <= 2 * rows) cands.push_back(sdfg_config{SDFG_KERNEL_SKEWED, k, L, 4});
+        if (try_resident) cands.push_back(sdfg_config{SDFG_KERNEL_RESIDENT, k, 0, 0});
+    }
+    float best_ms = 1e30f;
+    sdfg_config winner = {SDFG_KERNEL_TEMPORAL, default_depth(dtype), 0, 4};
+    for (const sdfg_config &c : cands) {
+        // warm-up, then timed
+        rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);
         if (rc != SDFG_OK) break;
-        if (try_resident) {
-            sdfg_config c = {SDFG_KERNEL_RESIDENT, k, 0, 0};
-            rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);
-            if (rc == SDFG_OK) {
-                cudaEventRecord(e0, s);
-                rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);
-                cudaEventRecord(e1, s);
-            }
-            if (rc == SDFG_OK && cudaEventSynchronize(e1) != cudaSuccess)
-                rc = cuda_error(cudaGetLastError(), "autotune sync");
-            if (rc != SDFG_OK) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) {
-                best_ms = ms;
-                winner = c;
-            }
+        cudaEventRecord(e0, s);
+        rc = run_single(a, b, rows, cols, ld, Tp, dtype, &c, false, s);
+        cudaEventRecord(e1, s);
+        if (rc != SDFG_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = cuda_error(cudaGetLastError(), "autotune sync");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            winner = c;
         }
     }
     cudaEventDestroy(e0);

@@ -202,8 +202,8 @@ struct Rec {
 std::mutex g_stats_mu;
 bool g_stats_on = false;
 std::vector<Rec> g_recs;
-const char *kFamilies[FAM_COUNT] = {"naive", "temporal", "persistent", "reduce", "copy",
-                                    "stencil3d", "sor", "resident", "skewed"};
+const char *kFamilies[FAM_COUNT] = {"naive", "temporal", "persistent", "reduce", "copy",   "stencil3d",
+                                    "sor",   "resident", "skewed",     "h2d",    "d2h"};
 }  // namespace
 
 static thread_local bool g_stats_suspended = false;

@@ -86,6 +86,8 @@ enum Family {
     FAM_SOR,
     FAM_RESIDENT,
     FAM_SKEWED,
+    FAM_H2D,  // host -> device copies of sdfg_jacobi2d_host
+    FAM_D2H,  // device -> host copies of sdfg_jacobi2d_host
     FAM_COUNT
 };
 TimedLaunch stats_begin(int family, cudaStream_t s);
@@ -116,7 +118,7 @@ int run_resident_passes(const void *src0, void *first, void *second, const std::
 
 // ---- skewed chains (skewed.cu) ------------------------------------------------
 // T steps of one grid in one launch of the chain kernel: passes of depth k,
-// chains of L rows (0: 1024), progress published every `pub` chunks (0: 4).
+// chains of L rows (0: 512), progress published every `pub` chunks (0: 12).
 // in/out must be TMA-compatible; in == out allowed.
 int run_single_chain(const void *in, void *out, int R, int C, int ld, long long T, int dtype, int k, int L, int pub,
                      DeviceState *st, cudaStream_t s);
