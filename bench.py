@@ -64,6 +64,13 @@ def parse():
     p.add_argument("--rho", type=float, default=0.9, help="serve: arrival rate as a fraction of served capacity")
     p.add_argument("--plain-seconds", type=float, default=120.0,
                    help="serve: wall-time cap of the plain-launch replay (a prefix of the trace)")
+    p.add_argument("--precision-grids", type=int, default=4, help="precision: 16384^2 grids per storage type")
+    p.add_argument("--line-requests", type=int, default=1000,
+                   help="default line: served requests (a prefix of the seeded 10,000-request trace)")
+    p.add_argument("--line-plain-seconds", type=float, default=90.0,
+                   help="default line: wall-time cap of the plain-launch replay")
+    p.add_argument("--no-extra-blocks", action="store_true",
+                   help="default line: skip the served, batch and precision blocks")
     return p.parse_args()
 
 
@@ -439,6 +446,17 @@ def run_ours(a):
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         cpu = cpu_oracle_sample(a, a.cpu_seconds)
+    # the rest of the metric and of the workload set, on one GPU: served
+    # p50/p99 against plain launches, the 512-grid batch, and the precision
+    # sweep's errors on every element (replicas at N > 1 run the line alone)
+    extra = {}
+    if world == 1 and not a.no_extra_blocks:
+        for key, fn in (("served", lambda: measure_serve(a, a.line_requests, a.rho, a.line_plain_seconds)),
+                        ("batch", lambda: measure_batch(a, 10, 3)),
+                        ("precision", lambda: measure_precision(a, a.precision_grids))):
+            t0 = time.perf_counter()
+            extra[key] = fn()
+            extra[key]["wall_s"] = time.perf_counter() - t0
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": max(3, a.warmup),
         "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -459,6 +477,7 @@ def run_ours(a):
                         "sdfg_jacobi2d_host; ms_per_step - copy - kernel is host-side overhead"},
         "clocks": clk.summary(),
         "gpu_launches": gpu_launches,
+        **extra,
     }))
     if dist is not None:
         dist.destroy_process_group()
@@ -471,12 +490,13 @@ def _padded(R, C, dtype, device="cuda"):
     return torch.zeros((R, ld), dtype=dtype, device=device)[:, :C]
 
 
-def run_batch(a):
+def measure_batch(a, steps: int, warmup: int):
     """512 uneven grids (rows, cols log-uniform in [64, 2048], T in [50, 500])
-    in ONE persistent launch, replayed through a captured CUDA graph."""
+    in ONE persistent launch, replayed through a captured CUDA graph; k and
+    the segment height from the project's batch autotuner unless --k or
+    --seg-rows fix them.  Returns the block of the JSON line."""
     import ctypes
 
-    import numpy as np
     import torch
 
     from paper_1902_10345_gb300 import binding, build, inputs
@@ -493,7 +513,7 @@ def run_batch(a):
         ys.append(y)
         descs.append(binding.desc_for(x, y, sp.T))
     updates = sum((sp.rows - 2) * (sp.cols - 2) * sp.T for sp in specs)
-    if a.k or a.seg_rows:
+    if a.k or (a.seg_rows and a.workload == "batch"):
         cfg = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=a.k or 8, seg_rows=a.seg_rows or 96,
                              warps=a.warps or 4)
         tuned = False
@@ -505,50 +525,57 @@ def run_batch(a):
     plan = ctypes.c_void_p()
     stream = torch.cuda.current_stream()
     binding.check(L.sdfg_batch_plan_create(ctypes.byref(plan), arr, len(descs), 64, ctypes.byref(cfg), 0))
-    for _ in range(max(3, a.warmup)):
+    for _ in range(max(3, warmup)):
         binding.check(L.sdfg_batch_plan_run(plan, stream.cuda_stream))
     binding.check(L.sdfg_batch_plan_results(plan, arr, len(descs)))
-    binding.sdfg_stats_reset()
-    binding.sdfg_stats_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(a.steps):
+        for _ in range(steps):
             binding.check(L.sdfg_batch_plan_run(plan, stream.cuda_stream))
         e1.record(stream)
         torch.cuda.synchronize()
-    binding.sdfg_stats_enable(False)
     binding.check(L.sdfg_batch_plan_results(plan, arr, len(descs)))
     ms = e0.elapsed_time(e1)
-    n_pk, ms_pk = binding.sdfg_stats_get("persistent")   # graph replays are not split per kernel
     binding.check(L.sdfg_batch_plan_destroy(plan))
-    value = updates * a.steps / (ms / 1e3) / 1e9
+    assert all(d.status == 0 and d.steps_done == sp.T for d, sp in zip(arr, specs))
+    value = updates * steps / (ms / 1e3) / 1e9
     k = cfg.k
     passes = sum(-(-sp.T // k) for sp in specs)
     bytes_per_step = sum((sp.rows - 2) * (sp.cols - 2) * 2 * 4 * -(-sp.T // k) for sp in specs)
     hbm, src = measured_peaks()
-    achieved = bytes_per_step / (ms / a.steps / 1e3) / 1e9
-    print(json.dumps({
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": max(3, a.warmup),
-        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+    achieved = bytes_per_step / (ms / steps / 1e3) / 1e9
+    del xs, ys
+    torch.cuda.empty_cache()
+    return {
+        "value": value, "unit": UNIT, "steps": steps, "warmup": max(3, warmup), "ms_per_step": ms / steps,
         "config": {"workload": "jacobi2d_batch512_uneven_f32", "grids": 512, "updates_per_step": updates,
                    "k": k, "seg_rows": cfg.seg_rows, "autotuned": tuned, "passes_per_step": passes,
+                   "kernel": "persistent (one launch per step, replayed from a captured CUDA graph)",
                    "layout": "each grid pitched to a multiple of 4 columns (16-byte rows)",
                    "l2": "1.3 GB resident, larger than L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": "persistent_kernel (graph replay; whole step timed)",
-                     "roofline_gupdates": hbm * k / 8},
-        "clocks": clk.summary(), "gpu_launches": 2 * a.steps,
-    }))
+                     "traffic": None, "peak_source": src, "roofline_gupdates": hbm * k / 8,
+                     "note": "algorithmic bytes 2 x 4 B per interior point and pass of k steps; whole step timed"},
+        "clocks": clk.summary(),
+    }
+
+
+def run_batch(a):
+    b = measure_batch(a, a.steps, a.warmup)
+    print(json.dumps({"metric": METRIC, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f32", "data": "synthetic", "gpu_launches": 2 * a.steps, **b}))
 
 
 # --------------------------------------------------------------- precision -------
-def run_precision(a):
-    """4 grids of 16384^2, T=500, sinusoid field; FP32 and BF16 storage.
-    Throughput of each, and the error of each result against the FP64 oracle
-    on light-cone windows (exact for the windows)."""
+def measure_precision(a, grids: int = 4):
+    """`grids` grids of 16384^2 (the sinusoid field), T = 500, with FP32
+    storage and with BF16 storage (FP32 arithmetic): throughput of each, and
+    each result's max-abs and RMS error against the FP64 oracle on EVERY
+    element.  The oracle starts from exactly the values the GPU received (the
+    field rounded to the storage type) and runs on all host threads; the
+    input's own rounding error is reported beside it."""
     import numpy as np
     import torch
 
@@ -557,13 +584,14 @@ def run_precision(a):
 
     build.build()
     binding.lib()
-    n, T, W = 16384, 500, 40
-    rng = np.random.default_rng(12345)
+    oracle.build()
+    n, T = 16384, 500
     out = {}
     stream = torch.cuda.current_stream()
+    oracle_s = 0.0
     for dt_name, tdt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
-        ms_total, errs, sq, cnt, q_err = 0.0, [], 0.0, 0, 0.0
-        for seed in range(4):
+        ms_total, max_err, sq, cnt, q_err = 0.0, 0.0, 0.0, 0, 0.0
+        for seed in range(grids):
             f64 = inputs.sinusoid_field_device(n, seed=seed)
             x = f64.to(tdt)
             q_err = max(q_err, float((x.double() - f64).abs().max()))
@@ -577,27 +605,31 @@ def run_precision(a):
             e1.record(stream)
             torch.cuda.synchronize()
             ms_total += e0.elapsed_time(e1)
-            for _ in range(3):
-                r0 = int(rng.integers(0, n - W))
-                c0 = int(rng.integers(0, n - W))
-                m = T + 1
-                cr0, cr1, cc0, cc1 = max(0, r0 - m), min(n, r0 + W + m), max(0, c0 - m), min(n, c0 + W + m)
-                crop = x[cr0:cr1, cc0:cc1].double().cpu().numpy()
-                want = oracle.jacobi2d(crop, T, threads=0)[r0 - cr0:r0 - cr0 + W, c0 - cc0:c0 - cc0 + W]
-                got = y[r0:r0 + W, c0:c0 + W].double().cpu().numpy()
-                d = got - want
-                errs.append(float(np.abs(d).max()))
-                sq += float((d * d).sum())
-                cnt += d.size
-            del x, y
+            xh = x.double().cpu().numpy()
+            t0 = time.perf_counter()
+            want = oracle.jacobi2d(xh, T, threads=0)
+            oracle_s += time.perf_counter() - t0
+            del xh
+            d = y.double().cpu().numpy()
+            d -= want
+            del want
+            max_err = max(max_err, float(np.abs(d).max()))
+            sq += float(np.einsum("ij,ij->", d, d))
+            cnt += d.size
+            del d, x, y
             torch.cuda.empty_cache()
-        updates = 4 * (n - 2) * (n - 2) * T
+        updates = grids * (n - 2) * (n - 2) * T
         out[dt_name] = {"gupdates_per_s": updates / (ms_total / 1e3) / 1e9, "ms": ms_total,
-                        "max_abs_err": max(errs), "rms_err": (sq / cnt) ** 0.5,
+                        "max_abs_err": max_err, "rms_err": (sq / cnt) ** 0.5,
                         "input_quantisation_max_abs": q_err,
-                        "windows": f"{len(errs)} windows of {W}x{W} (FP64 oracle on light-cone crops)"}
-    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "precision_4x16384sq_T500_sinusoid",
-                      "results": out, "tolerance": {"f32": 1e-4, "bf16": 2e-2}}))
+                        "compared": f"every element of {grids} grids of {n}x{n} (FP64 oracle, all host threads)"}
+    return {"workload": f"precision_{grids}x{n}sq_T{T}_sinusoid", "results": out,
+            "tolerance": {"f32": 1e-4, "bf16": 2e-2}, "oracle_seconds": oracle_s,
+            "kernel": "library default for the shape (chain kernel, k = 8)"}
+
+
+def run_precision(a):
+    print(json.dumps({"metric": METRIC, "unit": UNIT, **measure_precision(a, a.precision_grids)}))
 
 
 # ------------------------------------------------------------------- paper -------
@@ -847,13 +879,15 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v), q)) if len(v) else None
 
 
-def run_serve(a):
-    """Served Laplace solves: requests with sides log-uniform in [32, 4096],
-    boundary x^2 - y^2 + noise, zero interior, FP32, relative residual 1e-6 or
-    20000 steps, 40 GB budget.  Capacity first (all requests at t=0), then a
-    Poisson arrival trace at rho x capacity replayed against (1) the
-    continuous-batching server and (2) plain launches: one blocking solve per
-    request in arrival order."""
+def measure_serve(a, n: int, rho: float, plain_seconds: float):
+    """Served Laplace solves: the first n requests of the seeded served
+    trace (sides log-uniform in [32, 4096], boundary x^2 - y^2 + noise, zero
+    interior, FP32, relative residual 1e-6 or 20000 steps), 40 GB budget.
+    Capacity first (all requests at t = 0), then a Poisson arrival trace at
+    rho x capacity replayed against (1) the continuous-batching server and
+    (2) plain launches: one blocking sdfg_jacobi2d_solve per request in
+    arrival order, in the server's geometry (same fused depth and segment
+    height), so both stop every request at the same step: equal accuracy."""
     import ctypes
     import threading
 
@@ -864,21 +898,21 @@ def run_serve(a):
 
     build.build()
     L = binding.lib()
-    n = a.requests
     reqs = inputs.served_requests(n, seed=0)
     xs = [inputs.laplace_request_grid_device(r, dtype=torch.float32) for r in reqs]
     ys = [torch.zeros_like(x) for x in xs]
     tol, cap, stride, quantum = 1e-6, 20000, 64, 256
     budget = 40 << 30
+    # the server's geometry (its defaults unless --k / --seg-rows fix it)
+    k_srv = a.k or 4
+    seg_srv = a.seg_rows if (a.seg_rows and a.workload == "serve") else 96
+    geo = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=k_srv, seg_rows=seg_srv, warps=4)
 
     def serve(arrivals):
         sv = ctypes.c_void_p()
         binding.check(L.sdfg_server_create(ctypes.byref(sv), budget, 1024, quantum, stride, 0))
-        if a.k or a.seg_rows:
-            scfg = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=a.k, seg_rows=a.seg_rows)
-            binding.check(L.sdfg_server_set_config(sv, ctypes.byref(scfg)))
+        binding.check(L.sdfg_server_set_config(sv, ctypes.byref(geo)))
         ids = [None] * n
-        sub_t = [0.0] * n
         t0 = time.perf_counter()
 
         def submitter():
@@ -889,7 +923,6 @@ def run_serve(a):
                 d = binding.desc_for(xs[i], ys[i], cap, tol)
                 rid = ctypes.c_uint64()
                 binding.check(L.sdfg_server_submit(sv, ctypes.byref(d), ctypes.byref(rid)))
-                sub_t[i] = time.perf_counter()
                 ids[i] = rid.value
 
         th = threading.Thread(target=submitter)
@@ -934,7 +967,7 @@ def run_serve(a):
             if dt > 0:
                 time.sleep(dt)
             d = binding.desc_for(xs[i], ys[i], cap, tol)
-            binding.check(binding.sdfg_jacobi2d_solve(d, stride))
+            binding.check(binding.sdfg_jacobi2d_solve(d, stride, geo))
             done = time.perf_counter()
             lat.append(done - (t0 + arrivals[i]))
             steps.append(d.steps_done)
@@ -948,26 +981,35 @@ def run_serve(a):
     # capacity: everything queued at t = 0
     lat0, steps0, span0 = serve(np.zeros(n))
     capacity = n / span0
-    rate = a.rho * capacity
+    rate = rho * capacity
     arrivals = inputs.poisson_arrivals(n, rate, seed=1)
     lat_s, steps_s, span_s = serve(arrivals)
-    lat_p, steps_p, span_p, idx_p = plain(arrivals, a.plain_seconds)
+    lat_p, steps_p, span_p, idx_p = plain(arrivals, plain_seconds)
     # the server's latencies on the same prefix of the trace, for a like-for-like comparison
     lat_s_prefix = [lat_s[i] for i in idx_p]
-    print(json.dumps({
-        "metric": METRIC, "unit": UNIT, "workload": f"served_laplace_{n}req_32to4096_tol1e-6_cap20000_f32",
-        "capacity_req_per_s": capacity, "capacity_gupdates": gups(steps0, span0), "rho": a.rho,
+    del xs, ys
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"served_laplace_first{n}of10000req_32to4096_tol1e-6_cap20000_f32",
+        "requests": n, "capacity_req_per_s": capacity, "capacity_gupdates": gups(steps0, span0), "rho": rho,
         "arrival_rate_hz": rate,
         "server": {"p50_s": _pct(lat_s, 50), "p99_s": _pct(lat_s, 99), "gupdates": gups(steps_s, span_s),
                    "makespan_s": span_s},
         "plain_launches": {"p50_s": _pct(lat_p, 50), "p99_s": _pct(lat_p, 99),
                            "gupdates": gups(steps_p, span_p, idx_p), "requests_served": len(idx_p),
-                           "wall_cap_s": a.plain_seconds},
-        "server_on_same_prefix": {"p50_s": _pct(lat_s_prefix, 50), "p99_s": _pct(lat_s_prefix, 99)},
+                           "wall_cap_s": plain_seconds},
+        "server_on_same_prefix": {"p50_s": _pct(lat_s_prefix, 50), "p99_s": _pct(lat_s_prefix, 99),
+                                  "requests": len(idx_p)},
         "steps_equal_server_vs_plain": sum(int(steps_s[i] == s_) for i, s_ in zip(idx_p, steps_p)),
         "budget_bytes": budget, "quantum_steps": quantum, "check_stride": stride,
-        "server_config": {"k": a.k or 4, "seg_rows": a.seg_rows or 96},
-    }))
+        "geometry": {"k": k_srv, "seg_rows": seg_srv, "kernel": "persistent",
+                     "note": "server and plain launches run the same units, so every request stops at the "
+                             "same step on both paths"},
+    }
+
+
+def run_serve(a):
+    print(json.dumps({"metric": METRIC, "unit": UNIT, **measure_serve(a, a.requests, a.rho, a.plain_seconds)}))
 
 
 def main():

@@ -230,7 +230,7 @@ __device__ __forceinline__ bool chain_depth(int k, const void *tmap, ST *dst, co
 }
 
 #ifndef SDFG_CHAIN_PUB
-#define SDFG_CHAIN_PUB 4  // chunks between two progress updates of a chain
+#define SDFG_CHAIN_PUB 12  // chunks between two progress updates of a chain
 #endif
 #ifndef SDFG_CK_MINB
 #define SDFG_CK_MINB 3  // 128-thread CTAs per SM the register allocation must allow

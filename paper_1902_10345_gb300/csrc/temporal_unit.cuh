@@ -32,6 +32,8 @@
 // boundary, whose value is copied, so they never reach a stored result.
 #pragma once
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "geometry.h"
 
@@ -245,6 +247,9 @@ __device__ __noinline__ inline bool drain_after_timeout(uint64_t *bars, uint32_t
 #ifndef SDFG_RING2
 #define SDFG_RING2 1  // reassociated units keep two rows per level (level_p)
 #endif
+#ifndef SDFG_RES_FP64
+#define SDFG_RES_FP64 0  // residual: square and sum every difference in FP64 (else FP32 groups)
+#endif
 #ifndef SDFG_RING2_TURN
 #define SDFG_RING2_TURN 4  // rows per turn of the two-row-ring chunk loop
 #endif
@@ -295,7 +300,10 @@ struct UnitPipe {
     unsigned colmask, resmask;
     bool own_lane, full_vec;
     int res_flags;
-    CT g_ref, g_chk;  // group sums (at most CHUNK_ROWS rows of one lane)
+    // group sums (at most CHUNK_ROWS rows of one lane's V columns): in the
+    // storage type's arithmetic, or (SDFG_RES_FP64) every square in FP64
+    using RT = typename std::conditional<SDFG_RES_FP64 != 0, double, CT>::type;
+    RT g_ref, g_chk;
     double acc_ref, acc_chk;
     unsigned long long timeout_ns;
 
@@ -305,12 +313,12 @@ struct UnitPipe {
         tma_load_2d(ring + slot * (CHUNK_ROWS * W), tmap, X, rb + c * CHUNK_ROWS, &bars[slot]);
     }
 
-    __device__ __forceinline__ void accumulate(CT &g, const CT (&o)[V], const CT (&c)[V]) {
-        CT sum = CT(0);
+    __device__ __forceinline__ void accumulate(RT &g, const CT (&o)[V], const CT (&c)[V]) {
+        RT sum = RT(0);
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             if ((resmask >> e) & 1u) {
-                const CT d = o[e] - c[e];
+                const RT d = static_cast<RT>(o[e] - c[e]);  // the difference in the storage arithmetic
                 sum = fma(d, d, sum);
             }
         }
@@ -543,7 +551,7 @@ struct UnitPipe {
                     for (int e = 0; e < V; ++e) b[l][s][e] = CT(0);
         }
         if (RES) {
-            g_ref = g_chk = CT(0);
+            g_ref = g_chk = RT(0);
             acc_ref = acc_chk = 0.0;
         }
         int issued = 0;  // chunks whose load was issued
@@ -598,8 +606,8 @@ struct UnitPipe {
             if (RES) {
                 acc_ref += static_cast<double>(g_ref);
                 acc_chk += static_cast<double>(g_chk);
-                g_ref = CT(0);
-                g_chk = CT(0);
+                g_ref = RT(0);
+                g_chk = RT(0);
             }
         }
         return true;

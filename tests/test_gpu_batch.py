@@ -155,6 +155,26 @@ def test_solve_random_matches_oracle():
     assert abs(d.rel_residual - rel_o) <= 1e-3 * rel_o + 1e-9 or d.steps_done != steps_o
 
 
+@pytest.mark.parametrize("shape,tol,cap", [((90, 133), 1e-3, 40000), ((300, 260), 3e-2, 100000),
+                                           ((64, 70), 1e-6, 3000)])
+def test_solve_f64_residual_matches_oracle(shape, tol, cap):
+    """FP64 storage: the states equal the oracle's bit for bit, the residual
+    is squared and summed in FP64 from the first difference, so the stopping
+    step is the oracle's and the reported relative residual agrees with the
+    oracle's to FP64 rounding of the summation order (1e-12 relative)."""
+    R, C = shape
+    g = inputs.laplace_request_grid(inputs.Request(R, C, seed=11))
+    x = dev(g, F64)
+    y = torch.zeros_like(x)
+    stride = 32
+    d = binding.desc_for(x, y, cap, tol)
+    binding.check(binding.sdfg_jacobi2d_solve(d, stride))
+    want, steps_o, rel_o, _ = oracle.jacobi2d_tol(h64(x), cap, tol, stride, threads=0)
+    assert d.steps_done == steps_o, (d.steps_done, steps_o)
+    assert abs(d.rel_residual - rel_o) <= 1e-12 * rel_o, (d.rel_residual, rel_o)
+    assert np.array_equal(h64(y), want)
+
+
 def test_solve_bf16_invariants():
     """BF16 storage rounds the grid each time a pass stores it (every k
     steps), so on a Laplace solve with boundary values near +-1 (ulp 2^-7)
