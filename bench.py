@@ -425,7 +425,7 @@ def run_ours(a):
     ops_per_update, redundancy = fp32_lane_ops_per_update(fam, k_used, cfg.seg_rows)
     alu_achieved = ops_per_update * redundancy * value / 1e3
     from paper_1902_10345_gb300 import build as _b
-    digest = _b.kernel_digest()
+    digest = _b.kernel_digest(_b.KERNEL_FILES_CHAIN if fam == "skewed" else None)
     traffic = committed_traffic(digest, workload_name(a))
     gpu_launches = sum(v[0] for v in launches.values())
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

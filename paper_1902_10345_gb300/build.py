@@ -62,14 +62,15 @@ KERNEL_FILES = ["device_common.cuh", "temporal_unit.cuh", "geometry.h", "persist
 KERNEL_FILES_3D = ["device_common.cuh", "jacobi3d.cu"]
 KERNEL_FILES_SOR = ["device_common.cuh", "sor2d.cu"]
 KERNEL_FILES_RESIDENT = ["device_common.cuh", "resident.cu"]
+KERNEL_FILES_CHAIN = ["device_common.cuh", "temporal_unit.cuh", "geometry.h", "skewed.cu"]
 
 
 def kernel_digest(files=None) -> str:
     """Digest of the device sources and flags that define the kernels (used
     to tell whether a committed profile still describes the current kernels);
     files: the 2-D kernels' sources by default, KERNEL_FILES_3D,
-    KERNEL_FILES_SOR or KERNEL_FILES_RESIDENT for the 3-D, SOR and
-    register-resident ones."""
+    KERNEL_FILES_SOR, KERNEL_FILES_RESIDENT or KERNEL_FILES_CHAIN for the
+    3-D, SOR, register-resident and chain kernels."""
     h = hashlib.sha256()
     for f in files or KERNEL_FILES:
         with open(os.path.join(CSRC, f), "rb") as fh:
