@@ -514,8 +514,9 @@ def measure_batch(a, steps: int, warmup: int):
         descs.append(binding.desc_for(x, y, sp.T))
     updates = sum((sp.rows - 2) * (sp.cols - 2) * sp.T for sp in specs)
     if a.k or (a.seg_rows and a.workload == "batch"):
-        cfg = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=a.k or 8, seg_rows=a.seg_rows or 96,
-                             warps=a.warps or 4)
+        cfg = binding.config(kernel=kernel_code(binding, a.kernel if a.kernel in ("persistent", "skewed")
+                                                else "persistent"),
+                             k=a.k or 8, seg_rows=a.seg_rows or 96, warps=a.warps or 4)
         tuned = False
     else:
         # the project's autotuner picks k and the segment height on this batch
@@ -542,8 +543,11 @@ def measure_batch(a, steps: int, warmup: int):
     assert all(d.status == 0 and d.steps_done == sp.T for d, sp in zip(arr, specs))
     value = updates * steps / (ms / 1e3) / 1e9
     k = cfg.k
-    passes = sum(-(-sp.T // k) for sp in specs)
-    bytes_per_step = sum((sp.rows - 2) * (sp.cols - 2) * 2 * 4 * -(-sp.T // k) for sp in specs)
+    # passes of the plan: plan_passes(T, k) = T // k passes of k, then the remainder in powers of two
+    def n_passes(T):
+        return T // k + bin(T % k).count("1")
+    passes = sum(n_passes(sp.T) for sp in specs)
+    bytes_per_step = sum((sp.rows - 2) * (sp.cols - 2) * 2 * 4 * n_passes(sp.T) for sp in specs)
     hbm, src = measured_peaks()
     achieved = bytes_per_step / (ms / steps / 1e3) / 1e9
     del xs, ys
@@ -552,7 +556,8 @@ def measure_batch(a, steps: int, warmup: int):
         "value": value, "unit": UNIT, "steps": steps, "warmup": max(3, warmup), "ms_per_step": ms / steps,
         "config": {"workload": "jacobi2d_batch512_uneven_f32", "grids": 512, "updates_per_step": updates,
                    "k": k, "seg_rows": cfg.seg_rows, "autotuned": tuned, "passes_per_step": passes,
-                   "kernel": "persistent (one launch per step, replayed from a captured CUDA graph)",
+                   "kernel": ("chain kernel" if cfg.kernel == binding.SDFG_KERNEL_SKEWED else "persistent kernel")
+                             + " (one launch per step, replayed from a captured CUDA graph)",
                    "layout": "each grid pitched to a multiple of 4 columns (16-byte rows)",
                    "l2": "1.3 GB resident, larger than L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,

@@ -228,7 +228,16 @@ int sdfg_jacobi2d_batch(sdfg_desc *desc, int n, int check_stride, void *stream);
 
 /*
  * Batch plans: build once, replay many times.  The plan captures the
- * persistent launch (and its staging/finalise steps) in a CUDA graph.
+ * launches (and their staging/finalise steps) in a CUDA graph.  cfg->kernel:
+ * SDFG_KERNEL_PERSISTENT: every grid on the persistent kernel (fused depth
+ * cfg->k, segments of cfg->seg_rows rows); SDFG_KERNEL_SKEWED: fixed-step
+ * grids (tol = 0) of at least 2^20 points run as skewed chains of 512 rows
+ * at the library's depth (8 for FP32/BF16, 4 for FP64) in one launch, every
+ * other grid on the persistent kernel as above in a second launch; NULL: the
+ * batch autotuner's cached choice for this class of batch, else the
+ * persistent kernel.  Chains pay off for grids whose own work is long
+ * (measured on 16 grids of 2048^2, 496 steps: 5064 against 3321 GUpdates/s);
+ * on the uneven 512-grid batch the persistent kernel is faster.
  * plan_run is asynchronous; plan_results waits for the last run and fills
  * the outputs of desc[0..n-1] (the same order as at creation).
  */
@@ -329,11 +338,13 @@ int sdfg_sor2d(const void *in, void *out, int rows, int cols, int ld, int T, dou
  * scratch grids for the trials and frees them. */
 int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *best, void *stream);
 
-/* Batch autotuner: times candidate (k, segment height) plans of the
- * persistent kernel on the caller's batch (the grids are overwritten by the
- * trial runs), caches the best for batches of this class (dtype, grid count,
- * mean area), and returns it.  Plans created afterwards with cfg == NULL for
- * a batch of the same class use it. */
+/* Batch autotuner: times candidate plans on the caller's batch (the grids
+ * are overwritten by the trial runs): the persistent kernel at k = 4, 8 and
+ * several segment heights, and, when no grid has tol > 0, the chain kernel at
+ * k = 4, 8 for the large grids and the persistent kernel at 128- or 256-row
+ * segments for the others; caches the best for batches of this
+ * class (dtype, grid count, mean area), and returns it.  Plans created
+ * afterwards with cfg == NULL for a batch of the same class use it. */
 int sdfg_autotune_batch(const sdfg_desc *desc, int n, int check_stride, sdfg_config *best, void *stream);
 
 /* Per-kernel CUDA-event timing inside the library (off by default).  While
@@ -361,7 +372,11 @@ const char *sdfg_last_error(void);
  *           work item wait on a flag that nothing sets, so the bounded wait
  *           runs out and the launch reports SDFG_ERR_TIMEOUT;
  *   hook 2, value ns: limit of every bounded device wait in persistent
- *           launches created afterwards (0 = default, 2 s).
+ *           launches created afterwards (0 = default, 2 s);
+ *   hook 3, value n: batch plans created afterwards with SDFG_KERNEL_SKEWED
+ *           put fixed-step grids of at least n points on chains (-1 =
+ *           default, 2^20; 0 = every fixed-step grid);
+ *   hook 4, value L: chain length of those batch chains (0 = default, 512).
  */
 int sdfg_test_hook(int hook, long long value);
 

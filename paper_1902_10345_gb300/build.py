@@ -62,7 +62,7 @@ KERNEL_FILES = ["device_common.cuh", "temporal_unit.cuh", "geometry.h", "persist
 KERNEL_FILES_3D = ["device_common.cuh", "jacobi3d.cu"]
 KERNEL_FILES_SOR = ["device_common.cuh", "sor2d.cu"]
 KERNEL_FILES_RESIDENT = ["device_common.cuh", "resident.cu"]
-KERNEL_FILES_CHAIN = ["device_common.cuh", "temporal_unit.cuh", "geometry.h", "skewed.cu"]
+KERNEL_FILES_CHAIN = ["device_common.cuh", "temporal_unit.cuh", "geometry.h", "chain.cuh", "skewed.cu", "chain_batch.cu"]
 
 
 def kernel_digest(files=None) -> str:

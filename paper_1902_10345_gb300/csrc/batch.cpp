@@ -7,6 +7,7 @@
 #include <numeric>
 
 #include "autotune.h"
+#include "chainbatch.h"
 #include "launchset.h"
 
 namespace sdfg {
@@ -267,10 +268,16 @@ struct sdfg_batch_plan {
     std::vector<void *> owned;
     std::vector<int> staged_in;   // grid index of staged inputs
     std::vector<void *> staged_in_buf;
-    LaunchSet ls;
-    void *d_final = nullptr;
+    LaunchSet ls;            // grids on the persistent kernel
+    ChainBatch cb;           // large fixed-step grids on the skewed-chain kernel
+    std::vector<char> on_chain;
+    int n_pers = 0, n_chain = 0;
+    void *d_final = nullptr;  // finalise descriptors of the persistent grids
     int n_final = 0;
     int max_rows = 0;
+    void *d_gcopy = nullptr;  // result copies of the chain grids
+    int n_gcopy = 0;
+    int max_rows_gc = 0;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -293,10 +300,21 @@ static int plan_enqueue(sdfg_batch_plan *p, cudaStream_t s) {
                                     static_cast<size_t>(d.ld) * S, static_cast<size_t>(d.cols) * S, d.rows,
                                     cudaMemcpyDeviceToDevice, s));
     }
-    int rc = enqueue_persistent(p->ls, p->st, s);
-    if (rc != SDFG_OK) return rc;
-    if (p->n_final)
-        rc = launch_finalize(p->d_final, p->n_final, p->ls.L.grids, p->ls.L.state, p->dtype, p->max_rows, s);
+    // the chain grids first (their launch is the longer-lived), then the
+    // persistent grids, on the same stream
+    int rc = SDFG_OK;
+    if (p->n_chain) {
+        rc = p->cb.enqueue(p->st, s);
+        if (rc == SDFG_OK)
+            rc = launch_grid_copy(static_cast<const GridCopy *>(p->d_gcopy), p->n_gcopy, p->max_rows_gc, p->dtype, s);
+        if (rc != SDFG_OK) return rc;
+    }
+    if (p->n_pers) {
+        rc = enqueue_persistent(p->ls, p->st, s);
+        if (rc != SDFG_OK) return rc;
+        if (p->n_final)
+            rc = launch_finalize(p->d_final, p->n_final, p->ls.L.grids, p->ls.L.state, p->dtype, p->max_rows, s);
+    }
     return rc;
 }
 
@@ -308,7 +326,9 @@ static void plan_free(sdfg_batch_plan *p) {
     if (p->graph) cudaGraphDestroy(p->graph);
     for (void *b : p->owned) cudaFreeAsync(b, s);
     if (p->d_final) cudaFreeAsync(p->d_final, s);
+    if (p->d_gcopy) cudaFreeAsync(p->d_gcopy, s);
     p->ls.release(s);
+    p->cb.release(s);
     if (s) {
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
@@ -423,18 +443,62 @@ static int plan_build(sdfg_batch_plan **out, const sdfg_desc *desc, int n, int c
         run_of[g] = static_cast<int>(runs.size());
         runs.push_back(r);
     }
-    if (rc == SDFG_OK) rc = p->ls.build(runs);
+    // SDFG_KERNEL_SKEWED: large fixed-step grids on the chain kernel, every
+    // other grid on the persistent kernel (small grids keep more concurrent
+    // work in its per-unit wavefront than in chains of a few chunks)
+    const long long min_pts = test_hooks().chain_min_points >= 0 ? test_hooks().chain_min_points : (1LL << 20);
+    std::vector<GridRun> runs_c, runs_p;
+    std::vector<int> sub(n, -1);
+    p->on_chain.assign(n, 0);
+    for (int g = 0; g < n; ++g) {
+        if (run_of[g] < 0) continue;
+        const GridRun &r = runs[run_of[g]];
+        const bool ch = c.kernel == SDFG_KERNEL_SKEWED && r.tol == 0.0 && static_cast<long long>(r.R) * r.C >= min_pts;
+        p->on_chain[g] = ch ? 1 : 0;
+        sub[g] = static_cast<int>(ch ? runs_c.size() : runs_p.size());
+        (ch ? runs_c : runs_p).push_back(r);
+    }
+    p->n_chain = static_cast<int>(runs_c.size());
+    p->n_pers = static_cast<int>(runs_p.size());
+    if (rc == SDFG_OK && p->n_chain) {
+        p->cb.dtype = dtype;
+        // chains at the library's depth (8 for FP32/BF16): their long
+        // streamed units make the deepest fusion pay; cfg->k applies to the
+        // persistent part
+        p->cb.k = default_depth(dtype);
+        p->cb.L = test_hooks().chain_rows;
+        rc = p->cb.build(runs_c, s);
+        std::vector<GridCopy> gc;
+        for (int g = 0; g < n && rc == SDFG_OK; ++g) {
+            if (!p->on_chain[g]) continue;
+            const GridRun &r = runs_c[sub[g]];
+            const void *res = r.buf[p->cb.last_dst[sub[g]]];
+            if (res == desc[g].out) continue;
+            gc.push_back(GridCopy{res, desc[g].out, desc[g].rows, desc[g].cols, r.ld, desc[g].ld});
+            p->max_rows_gc = std::max(p->max_rows_gc, desc[g].rows);
+        }
+        if (rc == SDFG_OK && !gc.empty()) {
+            rc = scratch_alloc(&p->d_gcopy, gc.size() * sizeof(GridCopy), s);
+            if (rc == SDFG_OK) {
+                e = cudaMemcpyAsync(p->d_gcopy, gc.data(), gc.size() * sizeof(GridCopy), cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) rc = cuda_error(e, "batch plan upload");
+            }
+            p->n_gcopy = static_cast<int>(gc.size());
+        }
+    }
+    if (rc == SDFG_OK) rc = p->ls.build(runs_p);
     if (rc == SDFG_OK) {
         for (int g = 0; g < n; ++g) {
-            if (run_of[g] < 0) continue;
-            const int ri = run_of[g];
-            const bool staged = runs[ri].buf[0] != desc[g].out;
+            if (run_of[g] < 0 || p->on_chain[g]) continue;
+            const int ri = sub[g];
+            const bool staged = runs_p[ri].buf[0] != desc[g].out;
             const bool tol_mode = desc[g].tol > 0.0;
             if (!staged && !tol_mode && p->ls.last_dst[ri] == 0) continue;
             FinalDescHost f;
             f.src = nullptr;
             f.dst = desc[g].out;
-            f.ld_src = runs[ri].ld;
+            f.ld_src = runs_p[ri].ld;
             f.ld_dst = desc[g].ld;
             f.rows = desc[g].rows;
             f.cols = desc[g].cols;
@@ -444,8 +508,8 @@ static int plan_build(sdfg_batch_plan **out, const sdfg_desc *desc, int n, int c
             p->max_rows = std::max(p->max_rows, desc[g].rows);
         }
     }
-    if (rc == SDFG_OK) rc = p->ls.upload(s);
-    if (rc == SDFG_OK && !fin.empty()) {
+    if (rc == SDFG_OK && p->n_pers) rc = p->ls.upload(s);
+    if (rc == SDFG_OK && p->n_pers && !fin.empty()) {
         rc = scratch_alloc(&p->d_final, fin.size() * sizeof(FinalDescHost), s);
         if (rc == SDFG_OK) {
             e = cudaMemcpyAsync(p->d_final, fin.data(), fin.size() * sizeof(FinalDescHost), cudaMemcpyHostToDevice, s);
@@ -515,6 +579,8 @@ static int plan_results(sdfg_batch_plan *p, sdfg_desc *desc, int n) {
             desc[g].steps_done = 0;
         } else if (p->kind[g] == 1) {
             desc[g].steps_done = (d.rows < 3 || d.cols < 3) ? d.T : d.t_start;
+        } else if (p->on_chain[g]) {
+            desc[g].steps_done = d.T;  // fixed-step grids only
         } else {
             const PState &S = p->state_host[ri++];
             if (d.tol > 0.0) {
@@ -585,8 +651,10 @@ extern "C" int sdfg_jacobi2d_solve(sdfg_desc *desc, int check_stride, const sdfg
 }
 
 // ---------------------------------------------------------- batch tuner -----
-// Candidates: fused depth k in {4, 8} x segment height in {96, 128, 192,
-// 256, 384}.
+// Candidates: the persistent kernel at fused depth k in {4, 8} x segment
+// height in {96, 128, 192, 256, 384}, and, when no grid solves to a
+// tolerance, the hybrid (large grids on the chain kernel) at k in {4, 8} x
+// segment height in {128, 256}.
 // Each is built as a plan over the caller's batch, run once to warm up and
 // once timed; the fastest is cached under the batch's class (dtype, grid
 // count and mean area, both power-of-two buckets) and returned.
@@ -599,6 +667,17 @@ extern "C" int sdfg_autotune_batch(const sdfg_desc *desc, int n, int check_strid
     const int dtype = desc[0].dtype;
     const int ks[] = {4, 8};
     const int segs[] = {96, 128, 192, 256, 384};
+    bool any_tol = false;
+    for (int g = 0; g < n; ++g) any_tol |= desc[g].tol > 0.0;
+    std::vector<sdfg_config> cands;
+    for (int k : ks) {
+        if (dtype == SDFG_F64 && k > 4) continue;
+        for (int seg : segs) cands.push_back(sdfg_config{SDFG_KERNEL_PERSISTENT, k, seg, 4});
+        // large fixed-step grids on the chain kernel, the rest on the
+        // persistent kernel with this segment height
+        if (!any_tol)
+            for (int seg : {128, 256}) cands.push_back(sdfg_config{SDFG_KERNEL_SKEWED, k, seg, 4});
+    }
     float best_ms = 1e30f;
     sdfg_config winner = {SDFG_KERNEL_PERSISTENT, default_depth(dtype), 96, 4};
     std::vector<sdfg_desc> tmp(desc, desc + n);
@@ -606,31 +685,26 @@ extern "C" int sdfg_autotune_batch(const sdfg_desc *desc, int n, int check_strid
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = SDFG_OK;
-    for (int k : ks) {
-        if (dtype == SDFG_F64 && k > 4) continue;
-        for (int seg : segs) {
-            sdfg_config c = {SDFG_KERNEL_PERSISTENT, k, seg, 4};
-            sdfg_batch_plan *p = nullptr;
-            rc = plan_build(&p, desc, n, check_stride, &c, false);
-            if (rc != SDFG_OK) break;
-            cudaStream_t s = p->cap;
-            rc = plan_run(p, s);
-            if (rc == SDFG_OK) {
-                cudaEventRecord(e0, s);
-                rc = plan_run(p, s);
-                cudaEventRecord(e1, s);
-            }
-            if (rc == SDFG_OK) rc = plan_results(p, tmp.data(), n);
-            float ms = 0.f;
-            if (rc == SDFG_OK) cudaEventElapsedTime(&ms, e0, e1);
-            plan_free(p);
-            if (rc != SDFG_OK) break;
-            if (ms < best_ms) {
-                best_ms = ms;
-                winner = c;
-            }
-        }
+    for (const sdfg_config &c : cands) {
+        sdfg_batch_plan *p = nullptr;
+        rc = plan_build(&p, desc, n, check_stride, &c, false);
         if (rc != SDFG_OK) break;
+        cudaStream_t s = p->cap;
+        rc = plan_run(p, s);
+        if (rc == SDFG_OK) {
+            cudaEventRecord(e0, s);
+            rc = plan_run(p, s);
+            cudaEventRecord(e1, s);
+        }
+        if (rc == SDFG_OK) rc = plan_results(p, tmp.data(), n);
+        float ms = 0.f;
+        if (rc == SDFG_OK) cudaEventElapsedTime(&ms, e0, e1);
+        plan_free(p);
+        if (rc != SDFG_OK) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            winner = c;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -644,6 +718,8 @@ extern "C" int sdfg_test_hook(int hook, long long value) {
     switch (hook) {
         case 1: test_hooks().inject_stuck_wait = value ? 1 : 0; return SDFG_OK;
         case 2: test_hooks().timeout_ns = value > 0 ? static_cast<unsigned long long>(value) : 0; return SDFG_OK;
+        case 3: test_hooks().chain_min_points = value; return SDFG_OK;
+        case 4: test_hooks().chain_rows = value > 0 ? static_cast<int>(value) : 0; return SDFG_OK;
         default: return set_error(SDFG_ERR_INVAL, "unknown test hook %d", hook);
     }
 }

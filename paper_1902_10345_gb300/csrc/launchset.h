@@ -76,6 +76,8 @@ struct FinalDescHost {
 struct TestHooks {
     int inject_stuck_wait = 0;
     unsigned long long timeout_ns = 0;  // 0: default
+    long long chain_min_points = -1;    // batches: fixed-step grids of >= this many points go on chains (-1: 2^20)
+    int chain_rows = 0;                 // batches: chain length (0: 512)
 };
 TestHooks &test_hooks();
 

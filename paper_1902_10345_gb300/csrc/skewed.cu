@@ -18,34 +18,37 @@
 // shuffle exchange), as in the other kernels.
 //
 // Dependencies are per chunk.  A warp publishes, every `pub` chunks and at
-// the end, how many of its chain's rows are stored (a release store after a
-// warp barrier; the release waits for the warp's stores in flight, about a
+// the end, how many of its chain's rows are stored: a release store after a
+// warp barrier.  The release waits for the warp's stores in flight, about a
 // microsecond under full HBM traffic, so publishing after every chunk costs
 // ~13% and every 12 chunks ~2%, while a longer interval adds lag from pass to
-// pass: 12 chunks and 512-row chains are the measured best on 8192^2); before loading input rows [r0, r0 + CHUNK_ROWS) it waits
-// (bounded, acquire loads) until pass p-1 has stored those rows, plus
+// pass (12 chunks and 512-row chains are the measured best on 8192^2).
+// Before loading input rows [r0, r0 + CHUNK_ROWS) a warp waits (bounded,
+// acquire loads) until pass p-1 has stored those rows, plus
 // e = max(0, k_{p-1} - k_p) more, in strips s-1, s, s+1 (the first wait
 // starts e rows above the chain's first input row).  That also orders every
 // write after the reads of the previous pass that it overwrites: a chain of
 // pass p-1 that reads row r either lies within the rows waited for, and is
-// then complete, or holds the last row waited for, and has then loaded
-// every row up to it plus k_{p-1}, which includes r.  Work items (pass, chain, strip) are dequeued with one atomic add each,
-// pass-major, and an item only waits on items dequeued before it, so there
-// is no deadlock.
+// then complete, or holds the last row waited for, and has then loaded every
+// row up to it plus k_{p-1}, which includes r.  Work items (pass, chain,
+// strip) are dequeued with one atomic add each, pass-major, and an item only
+// waits on items dequeued before it, so there is no deadlock.
 //
-// Units away from the boundary columns use the reassociated pipe, also in the
-// first and last chain of a strip: rows 0 and R-1 are handled by the pipe's
-// edge body and never stored; the host copies them into both ping-pong grids
-// before the launch.  Units on the boundary columns keep the exact order.
+// FP32 and BF16 storage use the reassociated pipe everywhere, also in the
+// first and last chain of a strip and on the boundary strips: the boundary
+// ring (rows 0 and R-1, columns 0 and C-1) is held scaled like every other
+// value and never stored; a small kernel copies the ring into both ping-pong
+// grids before the launch.  FP64 keeps the exact order and stores the ring.
 #include <limits.h>
 #include <string.h>
 
 #include <algorithm>
 #include <mutex>
 
+#include "chain.cuh"
+#include "chainbatch.h"
 #include "launchset.h"
 #include "runtime.h"
-#include "temporal_unit.cuh"
 
 namespace sdfg {
 
@@ -70,168 +73,6 @@ struct ChainParams {
     unsigned long long timeout_ns;
 };
 
-__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
-
-// Spin (lane-parallel) until every lane's predicate holds; false on timeout.
-template <class Pred>
-__device__ __forceinline__ bool chain_warp_wait(Pred pred, unsigned long long timeout_ns) {
-    if (__all_sync(FULL_MASK, pred())) return true;
-    const unsigned long long t0 = globaltimer_ns();
-    while (true) {
-        __nanosleep(64);
-        if (__all_sync(FULL_MASK, pred())) return true;
-        const bool late = globaltimer_ns() - t0 > timeout_ns;
-        if (__any_sync(FULL_MASK, late)) return false;
-    }
-}
-
-// Collective (whole warp): wait until pass p-1 has stored rows [from,
-// need_hi] in the strips s-1, s, s+1.  Returns the largest row up to which
-// that is now known (>= need_hi), or INT_MIN if a bounded wait ran out (the
-// error word is set).  Out of line: a chain reaches it only when the
-// producer's last known progress is not enough.
-__device__ __noinline__ int chain_wait_rows(const int *prog_prev, int beta_prev, int jmin_prev, int L, int R,
-                                            int n_strips, int s, int from, int need_hi, int *err,
-                                            unsigned long long timeout_ns) {
-    const int lane = threadIdx.x & 31;
-    const int ja = floor_div(from - beta_prev, L);
-    const int jb = floor_div(need_hi - beta_prev, L);
-    const int s2 = s + lane - 1;
-    const bool mine = lane < 3 && s2 >= 0 && s2 < n_strips;
-    int seen = INT_MAX;
-    for (int jj = ja; jj <= jb; ++jj) {
-        const int lo = max(0, jj * L + beta_prev);
-        const int need = (jj < jb) ? min(R, (jj + 1) * L + beta_prev) - lo : need_hi - lo + 1;
-        const int *f = prog_prev + (jj - jmin_prev) * n_strips + s2;  // dereferenced by `mine` lanes only
-        int v = INT_MAX;
-        const bool good = chain_warp_wait(
-            [&] {
-                if (!mine) return true;
-                v = ld_acquire_gpu(f);
-                return v >= need;
-            },
-            timeout_ns);
-        if (!good) {
-            if (lane == 0) set_device_error(err, DEV_ERR_TIMEOUT_DEP);
-            return INT_MIN;
-        }
-        if (jj == jb) seen = static_cast<int>(__reduce_min_sync(FULL_MASK, static_cast<unsigned>(mine ? v : INT_MAX)));
-    }
-    // the acquiring lanes' view reaches lane 0 through the barrier; lane 0
-    // then orders it before its TMA (async proxy) reads
-    __syncwarp();
-    if (lane == 0) fence_proxy_async_global();
-    return max(0, jb * L + beta_prev) + seen - 1;
-}
-
-// UnitPipe hook of one chain: waits on pass p-1's progress before each chunk
-// load, publishes this chain's progress after its chunks.
-struct ChainHook {
-    static constexpr bool EDGES = true;
-    const int *prog_prev;  // counters of pass p-1 (nullptr for pass 0: the input is ready)
-    int *prog_own;         // this chain's counter
-    int beta_prev, jmin_prev, L, R, n_strips, s, lane;
-    int rb, extra, ok_hi;  // ok_hi: rows <= ok_hi of pass p-1 are known stored in strips s-1..s+1
-    int y0, y1, K, n_chunks, pub;
-    int *err;
-    unsigned long long timeout_ns;
-
-    // Collective: pass p-1's rows up to the end of chunk c (plus `extra`) are
-    // stored in the three strips around s.
-    __device__ __forceinline__ bool ready(int c) {
-        if (!prog_prev) return true;
-        const int r0 = rb + c * CHUNK_ROWS;
-        const int need_hi = min(R - 1, r0 + CHUNK_ROWS - 1 + extra);
-        if (need_hi <= ok_hi) return true;
-        ok_hi = chain_wait_rows(prog_prev, beta_prev, jmin_prev, L, R, n_strips, s, ok_hi + 1, need_hi, err,
-                                timeout_ns);
-        return ok_hi != INT_MIN;
-    }
-
-    // Chunk c's rows are stored and the warp is synchronised: publish every
-    // `pub` chunks and at the end.
-    __device__ __forceinline__ void done(int c) {
-        if (c != n_chunks - 1 && (c + 1) % pub != 0) return;
-        const int r0 = rb + c * CHUNK_ROWS;
-        const int v = max(0, min(r0 + CHUNK_ROWS - K, y1) - y0);
-        if (lane == 0) st_release_gpu(prog_own, v);
-    }
-};
-
-// One chain: output rows [lo, hi) of strip s, read through `tmap`, written to dst.
-template <class ST, int V, int K>
-__device__ __forceinline__ bool run_chain(const void *tmap, ST *dst, const GridGeo &g, int s, int lo, int hi,
-                                          ST *ring, uint64_t *bars, uint32_t &chunk_ctr, ChainHook &hk,
-                                          unsigned long long timeout_ns) {
-    constexpr int W = 32 * V;
-    const int lane = threadIdx.x & 31;
-    const int X = s * g.wout - g.h;
-    const int rb = max(0, lo - K);
-    const int n_steps = hi + K - rb;
-    const int n_chunks = (n_steps + CHUNK_ROWS - 1) / CHUNK_ROWS;
-    const int gc0 = X + lane * V;
-    const int hl = g.h / V;
-    unsigned colmask = 0;
-#pragma unroll
-    for (int e = 0; e < V; ++e) {
-        const int gc = gc0 + e;
-        if (gc <= 0 || gc >= g.C - 1) colmask |= 1u << e;
-    }
-    const bool own_lane = lane >= hl && lane < 32 - hl && gc0 < g.C;
-    const bool full_vec = gc0 + V <= g.C;
-    const bool colchk = (X <= 0) || (X + W > g.C - 1);
-    hk.rb = rb;
-    // The first wait starts `extra` rows above the first input row: when
-    // pass p-1 fused more steps than pass p, its chain that ends at row rb
-    // still reads up to extra - 1 rows into this chain's output rows, so it
-    // must be complete before they are written.
-    hk.ok_hi = max(0, rb - hk.extra) - 1;
-    hk.y0 = lo;
-    hk.y1 = hi;
-    hk.K = K;
-    hk.n_chunks = n_chunks;
-    bool ok;
-#define SDFG_CHAIN_PIPE(CHK, EX, SY0, SY1)                                                              \
-    {                                                                                                   \
-        UnitPipe<ST, V, K, CHK, false, EX> p;                                                           \
-        p.tmap = tmap; p.dst = dst; p.ld = g.ld; p.R = g.R; p.C = g.C;                                  \
-        p.X = X; p.y0 = lo; p.y1 = hi; p.rb = rb; p.n_steps = n_steps; p.n_chunks = n_chunks;           \
-        p.sy0 = (SY0); p.sy1 = (SY1);                                                                   \
-        p.base = chunk_ctr; p.ring = ring; p.bars = bars; p.lane = lane;                                \
-        p.colmask = colmask; p.resmask = 0; p.own_lane = own_lane; p.full_vec = full_vec;               \
-        p.res_flags = 0; p.timeout_ns = timeout_ns;                                                     \
-        ok = p.run(hk);                                                                                 \
-    }
-    // the reassociated pipe needs its two-row ring to handle rows 0 and R-1
-    constexpr bool SCALED_OK = UnitPipe<ST, V, K, false, false, false>::RING2;
-    if (colchk || !SCALED_OK) {
-        if (colchk)
-            SDFG_CHAIN_PIPE(true, true, lo, hi)
-        else
-            SDFG_CHAIN_PIPE(false, true, lo, hi)
-    } else {
-        SDFG_CHAIN_PIPE(false, false, max(lo, 1), min(hi, g.R - 1))
-    }
-#undef SDFG_CHAIN_PIPE
-    chunk_ctr += static_cast<uint32_t>(n_chunks);
-    return ok;
-}
-
-template <class ST, int V>
-__device__ __forceinline__ bool chain_depth(int k, const void *tmap, ST *dst, const GridGeo &g, int s, int lo, int hi,
-                                            ST *ring, uint64_t *bars, uint32_t &ctr, ChainHook &hk,
-                                            unsigned long long timeout_ns) {
-    switch (k) {
-        case 1: return run_chain<ST, V, 1>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
-        case 2: return run_chain<ST, V, 2>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
-        case 4: return run_chain<ST, V, 4>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
-        default: return run_chain<ST, V, 8>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
-    }
-}
-
-#ifndef SDFG_CHAIN_PUB
-#define SDFG_CHAIN_PUB 12  // chunks between two progress updates of a chain
-#endif
 #ifndef SDFG_CK_MINB
 #define SDFG_CK_MINB 3  // 128-thread CTAs per SM the register allocation must allow
 #endif
@@ -325,6 +166,7 @@ struct ChainPlan {
     void *scratch = nullptr;
     void *slab = nullptr;
     size_t const_bytes = 0, slab_bytes = 0;
+    const void *ring = nullptr;  // the ring-copy descriptor (inside the slab)
     int last = 0;      // buffer written by the last pass
     int blocks = 0;    // CTAs
     ChainParams prm{};
@@ -374,7 +216,8 @@ int chain_plan_build(ChainPlan *c, DeviceState *st, cudaStream_t s) {
     const size_t o_beta = al(o_k + P * sizeof(int));
     const size_t o_jmin = al(o_beta + P * sizeof(int));
     const size_t o_off = al(o_jmin + P * sizeof(int));
-    const size_t o_prog = al(o_off + P * sizeof(int));
+    const size_t o_ring = al(o_off + P * sizeof(int));
+    const size_t o_prog = al(o_ring + sizeof(RingCopy));
     const size_t o_head = al(o_prog + static_cast<size_t>(n_prog) * sizeof(int));
     const size_t total_bytes = al(o_head + sizeof(int));
     int rc = scratch_alloc(&c->slab, total_bytes, s);
@@ -385,9 +228,23 @@ int chain_plan_build(ChainPlan *c, DeviceState *st, cudaStream_t s) {
     memcpy(img.data() + o_beta, beta.data(), P * sizeof(int));
     memcpy(img.data() + o_jmin, jmin.data(), P * sizeof(int));
     memcpy(img.data() + o_off, off.data(), P * sizeof(int));
+    {
+        // the input's boundary ring into both ping-pong grids (the
+        // reassociated units never store it)
+        RingCopy rcp{};
+        rcp.src = c->in;
+        int nd = 0;
+        if (c->out != c->in) rcp.dst[nd++] = c->out;
+        rcp.dst[nd++] = c->scratch;
+        rcp.R = R;
+        rcp.C = c->C;
+        rcp.ld = c->ld;
+        memcpy(img.data() + o_ring, &rcp, sizeof(rcp));
+    }
     SDFG_CUDA(cudaMemcpyAsync(c->slab, img.data(), img.size(), cudaMemcpyHostToDevice, s));
     SDFG_CUDA(cudaStreamSynchronize(s));  // the host image must outlive the copy
     c->const_bytes = o_prog;
+    c->ring = static_cast<unsigned char *>(c->slab) + o_ring;
     c->slab_bytes = total_bytes;
     unsigned char *base = static_cast<unsigned char *>(c->slab);
     ChainParams &q = c->prm;
@@ -477,15 +334,10 @@ int run_single_chain(const void *in, void *out, int R, int C, int ld, long long 
         g_chain.push_back(c);
     }
     c->stamp = ++g_chain_clock;
-    const size_t S = dtype_bytes(dtype);
-    // the reassociated units never store rows 0 and R-1: both ping-pong grids
-    // hold them before the launch (one 2-row copy per grid that is not `in`)
-    for (int b = 0; b < 2; ++b) {
-        void *d = c->prm.buf[b];
-        if (d == in) continue;
-        SDFG_CUDA(cudaMemcpy2DAsync(d, static_cast<size_t>(R - 1) * ld * S, in, static_cast<size_t>(R - 1) * ld * S,
-                                    C * S, 2, cudaMemcpyDeviceToDevice, s));
-    }
+    // the reassociated units never store the boundary ring: both ping-pong
+    // grids receive it from the input before the launch
+    int rc = launch_ring_copy(static_cast<const RingCopy *>(c->ring), 1, 2 * C + 2 * (R - 2), dtype, s);
+    if (rc != SDFG_OK) return rc;
     unsigned char *base = static_cast<unsigned char *>(c->slab);
     SDFG_CUDA(cudaMemsetAsync(base + c->const_bytes, 0, c->slab_bytes - c->const_bytes, s));
     ChainParams prm = c->prm;

@@ -327,10 +327,24 @@ struct UnitPipe {
 
     // Store one output row at `p` (= row start + X + lane*V).  Away from
     // the boundary columns every owned lane holds V in-grid columns, so the
-    // store is one predicated vector instruction.
+    // store is one predicated vector instruction.  The reassociated pipe on
+    // a boundary strip (RING2 with COLCHK) never stores the boundary
+    // columns: the caller provides them in the destination grid.
     __device__ __forceinline__ void store_row(ST *p, const CT (&o)[V]) {
         if (!COLCHK) {
             store_pred(p, o, own_lane ? 1 : 0);
+        } else if (RING2) {
+            if (own_lane) {
+                if (colmask == 0u) {
+                    VecIO<ST, V>::store(p, o);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const int gc = X + lane * V + e;
+                        if (gc >= 1 && gc <= C - 2) p[e] = from_ct<ST>(o[e]);
+                    }
+                }
+            }
         } else if (own_lane) {
             if (full_vec) {
                 VecIO<ST, V>::store(p, o);
@@ -446,7 +460,8 @@ struct UnitPipe {
     // value, which a level holds scaled like every other row (5^l times the
     // state, each factor 5 rounded once), so its neighbours' sums stay
     // consistent; such rows are never stored by this pipe (sy0 >= 1,
-    // sy1 <= R-1): the caller provides them in the destination grid.
+    // sy1 <= R-1): the caller provides them in the destination grid.  With
+    // COLCHK the same holds for columns 0 and C-1 of a boundary strip.
     template <bool EDGE>
     __device__ __forceinline__ void step2(int r, const ST *src, ST *out) {
         CT x[V];
@@ -455,7 +470,7 @@ struct UnitPipe {
         for (int l = 0; l < K; ++l) {
             CT o[V];
             CT cen[V];  // the centre row (for the residual sums and the boundary)
-            if (RES || EDGE) {
+            if (RES || EDGE || COLCHK) {
 #pragma unroll
                 for (int e = 0; e < V; ++e) cen[e] = ra[l][e];
             }
@@ -469,6 +484,13 @@ struct UnitPipe {
 #pragma unroll
                     for (int e = 0; e < V; ++e) o[e] = __fmul_rn(5.0f, cen[e]);
                 }
+            }
+            if (COLCHK) {
+                // boundary columns (and columns outside the grid, which only
+                // ever feed them) keep their value, scaled like the rows
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    if ((colmask >> e) & 1u) o[e] = __fmul_rn(5.0f, cen[e]);
             }
             if (l == K - 1) scale_last<(K == 1 ? PAIRS0 : PAIRS_SPLIT)>(o);
             if (RES && l == 0 && (res_flags & 1)) {

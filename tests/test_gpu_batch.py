@@ -1,6 +1,6 @@
-"""Persistent-kernel paths through the C ABI: batches of uneven grids, CUDA
-graph replay, tolerance solves (data-dependent stop), the bounded-wait
-failure path, and the single-grid persistent kernel.
+"""Batch paths through the C ABI: batches of uneven grids on the persistent
+and on the chain kernel, CUDA graph replay, tolerance solves (data-dependent
+stop), the bounded-wait failure path, and the single-grid persistent kernel.
 
 Every result is compared with the FP64 oracle; fixed-step results must also
 equal the single-grid temporal kernel bit for bit (the same order of
@@ -91,6 +91,101 @@ def test_batch_fixed_steps_matches_oracle_and_single_kernel():
         got = h64(y)
         assert np.abs(got - want).max() <= TOL[F32], (i, np.abs(got - want).max())
         assert torch.equal(y, ref[i]), f"grid {i}: batch and single-grid kernels disagree"
+
+
+def _plan_run(descs, cfg, runs=1):
+    """Build a plan over `descs` with `cfg`, run it `runs` times, fill the outputs."""
+    import ctypes
+    L = binding.lib()
+    arr = (binding.sdfg_desc * len(descs))(*descs)
+    plan = ctypes.c_void_p()
+    binding.check(L.sdfg_batch_plan_create(ctypes.byref(plan), arr, len(descs), 64, ctypes.byref(cfg), 0))
+    try:
+        for _ in range(runs):
+            binding.check(L.sdfg_batch_plan_run(plan, torch.cuda.current_stream().cuda_stream))
+        binding.check(L.sdfg_batch_plan_results(plan, arr, len(descs)))
+    finally:
+        binding.check(L.sdfg_batch_plan_destroy(plan))
+    torch.cuda.synchronize()
+    assert binding.sdfg_device_error(True) == 0
+    return list(arr)
+
+
+@pytest.mark.parametrize("k,L", [(8, 512), (8, 32), (4, 24), (2, 16)])
+@pytest.mark.parametrize("dt", [F32, BF16, F64])
+def test_chain_batch_matches_oracle(k, L, dt):
+    """Fixed-step batches on the chain kernel: uneven grids (tiny, non-square,
+    one pitched, one unaligned and so staged, one in place, one with T = 0),
+    step counts with remainder passes, short chains so that grids hold several
+    chains; every grid whole against the FP64 oracle (FP64 bit for bit), and
+    a second run of the same plan gives the same bits."""
+    if dt == F64 and k > 4:
+        k = 4
+    xs, ys, descs, specs = [], [], [], make_batch(3)
+    for i, (g, ld, T) in enumerate(specs):
+        x = dev(g, dt, ld)
+        y = x if i == 5 else alloc_like(x)
+        x0 = x.clone() if i == 5 else x
+        xs.append(x0)
+        ys.append(y)
+        descs.append(binding.desc_for(x, y, T))
+    cfg = binding.config(kernel=binding.SDFG_KERNEL_SKEWED, k=k, seg_rows=96)
+    binding.check(binding.sdfg_test_hook(3, 0))      # every fixed-step grid on chains ...
+    binding.check(binding.sdfg_test_hook(4, L))      # ... of L rows
+    try:
+        out = _plan_run(descs, cfg)
+        firsts = [y.clone() for y in ys]
+        ys[5].copy_(xs[5])                           # grid 5 is in place: restore its input
+        _plan_run(descs, cfg)                        # and replay
+    finally:
+        binding.sdfg_test_hook(3, -1)
+        binding.sdfg_test_hook(4, 0)
+    for a, b in zip(firsts, ys):
+        assert torch.equal(a, b)
+    for i, ((g, ld, T), x, y, d) in enumerate(zip(specs, xs, ys, out)):
+        assert d.status == 0 and d.steps_done == T
+        want = oracle.jacobi2d(h64(x), T)
+        err = np.abs(h64(y) - want).max()
+        if dt == F64:
+            assert np.array_equal(h64(y), want), (i, err)
+        else:
+            assert err <= TOL[dt], (i, (g.shape, ld, T), err)
+        # the boundary ring comes out exact
+        assert torch.equal(y[0], x[0]) and torch.equal(y[-1], x[-1])
+        assert torch.equal(y[:, 0], x[:, 0]) and torch.equal(y[:, -1], x[:, -1])
+
+
+def test_hybrid_batch_with_tolerance_grids():
+    """SDFG_KERNEL_SKEWED on a mixed batch: fixed-step grids above the size
+    threshold on chains, the rest (and every tolerance solve) on the
+    persistent kernel, in one plan; each result against the oracle, and each
+    tolerance solve equal to the same solve alone on the persistent kernel."""
+    specs = make_batch(5)
+    xs, ys, descs = [], [], []
+    for i, (g, ld, T) in enumerate(specs):
+        x = dev(g, F32, ld)
+        xs.append(x)
+        ys.append(alloc_like(x))
+        descs.append(binding.desc_for(x, ys[-1], T + 200, 1e-3) if i % 3 == 0 else binding.desc_for(x, ys[-1], T))
+    cfg = binding.config(kernel=binding.SDFG_KERNEL_SKEWED, k=8, seg_rows=96)
+    binding.check(binding.sdfg_test_hook(3, 10000))  # grids of >= 10000 points on chains
+    binding.check(binding.sdfg_test_hook(4, 64))
+    try:
+        out = _plan_run(descs, cfg)
+    finally:
+        binding.sdfg_test_hook(3, -1)
+        binding.sdfg_test_hook(4, 0)
+    for i, ((g, ld, T), x, y, d) in enumerate(zip(specs, xs, ys, out)):
+        assert d.status == 0
+        want = oracle.jacobi2d(h64(x), d.steps_done)
+        assert np.abs(h64(y) - want).max() <= TOL[F32], i
+        if i % 3 == 0 and min(g.shape) >= 3:
+            alone = alloc_like(x)
+            da = binding.desc_for(x, alone, T + 200, 1e-3)
+            binding.check(binding.sdfg_jacobi2d_solve(da, 64, binding.config(kernel=3, k=8, seg_rows=96)))
+            assert da.steps_done == d.steps_done and torch.equal(alone, y), i
+        elif min(g.shape) >= 3:
+            assert d.steps_done == T
 
 
 def test_batch_plan_graph_replay():
@@ -263,12 +358,17 @@ def test_persistent_single_grid_equals_temporal(shape, T):
             assert torch.equal(y, ref)
 
 
-def test_full_512_grid_batch_in_the_bench_configuration():
+@pytest.mark.parametrize("kernel,k,seg,min_pts", [("persistent", 4, 256, -1), ("skewed", 8, 256, -1),
+                                                  ("skewed", 4, 128, -1), ("skewed", 8, 256, 0)])
+def test_full_512_grid_batch_in_the_bench_configuration(kernel, k, seg, min_pts):
     """The benchmark's batch (512 uneven grids, rows and columns log-uniform
     in [64, 2048], T in [50, 500], each grid pitched to 16-byte rows) in the
-    configuration it measures (one persistent launch, k = 4, 256-row
-    segments, replayed from a plan): every grid runs exactly T steps, and
-    every one of the 512 results matches the FP64 oracle on every element."""
+    configurations its autotuner chooses between, replayed from a plan: the
+    persistent kernel at k = 4 with 256-row segments; the hybrid (grids of
+    >= 2^20 points on 512-row chains, the rest on the persistent kernel) at
+    k = 8 and k = 4; and every grid on chains:
+    every grid runs exactly T steps, and every one of the 512 results matches
+    the FP64 oracle on every element."""
     import ctypes
     specs = inputs.batch_specs(512, seed=0)
     xs, ys, descs = [], [], []
@@ -282,13 +382,16 @@ def test_full_512_grid_batch_in_the_bench_configuration():
         descs.append(binding.desc_for(x, y, sp.T))
     L = binding.lib()
     arr = (binding.sdfg_desc * len(descs))(*descs)
-    cfg = binding.config(kernel=binding.SDFG_KERNEL_PERSISTENT, k=4, seg_rows=256, warps=4)
+    kern = binding.SDFG_KERNEL_PERSISTENT if kernel == "persistent" else binding.SDFG_KERNEL_SKEWED
+    cfg = binding.config(kernel=kern, k=k, seg_rows=seg, warps=4)
     plan = ctypes.c_void_p()
-    binding.check(L.sdfg_batch_plan_create(ctypes.byref(plan), arr, len(descs), 64, ctypes.byref(cfg), 0))
+    binding.check(binding.sdfg_test_hook(3, min_pts))
     try:
+        binding.check(L.sdfg_batch_plan_create(ctypes.byref(plan), arr, len(descs), 64, ctypes.byref(cfg), 0))
         binding.check(L.sdfg_batch_plan_run(plan, torch.cuda.current_stream().cuda_stream))
         binding.check(L.sdfg_batch_plan_results(plan, arr, len(descs)))
     finally:
+        binding.sdfg_test_hook(3, -1)
         binding.check(L.sdfg_batch_plan_destroy(plan))
     torch.cuda.synchronize()
     assert binding.sdfg_device_error(True) == 0
