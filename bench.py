@@ -657,7 +657,7 @@ def run_paper(a):
     x = torch.from_numpy(g).float().cuda()
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
-    if a.k or a.seg_rows or a.kernel != "persistent":
+    if a.k or a.seg_rows:
         cfg = binding.config(kernel=kernel_code(binding, a.kernel), k=a.k or 8, seg_rows=a.seg_rows,
                              warps=a.warps or 4)
     else:
