@@ -28,11 +28,14 @@
 // row is kept.  Boundary-ring points and points outside the grid keep their
 // values.  BF16 storage is converted to FP32 at the box load and rounded to
 // BF16 (RNE) when the pass stores the tile.
+#include <string.h>
+
 #include <algorithm>
 #include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
+#include "launchset.h"
 #include "runtime.h"
 
 namespace sdfg {
@@ -57,7 +60,7 @@ constexpr int RS_BOX_ROWS = RS_BY / 2;          // rows per TMA copy (<= 256)
 
 struct ResGeo {
     int R, C, ld;
-    int tiles_x;
+    int tiles_x, tiles_y;
 };
 
 template <int I, int N, class F> __device__ __forceinline__ void rs_static_for(F &&f) {
@@ -78,10 +81,18 @@ __device__ __forceinline__ void rs_west_east(float (&we)[4], const float (&c)[4]
     we[3] = __fadd_rn(c[2], right);
 }
 
+// Launch parameters of one pass: read through tm, write dst, fuse k steps.
+struct ResParams {
+    CUtensorMap tm;
+    void *dst;
+    ResGeo g;
+    int k;
+    int *err;
+    unsigned long long timeout_ns;
+};
+
 template <class ST>
-__global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __grid_constant__ CUtensorMap tm,
-                                                                     ST *__restrict__ dst, const ResGeo g, int k,
-                                                                     int *err, unsigned long long timeout_ns) {
+__global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __grid_constant__ ResParams P) {
     constexpr int V = 4;
     constexpr uint32_t BOX_BYTES = RS_BY * RS_W * sizeof(ST);
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -93,6 +104,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
     __shared__ __align__(16) float bot[2][RS_NW + 1][RS_W];
     ST *box = reinterpret_cast<ST *>(smem_raw);
 
+    const ResGeo g = P.g;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
@@ -102,11 +114,12 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
     const int y0 = ty * RS_TY;                // first output row
     // box row r <-> grid row y0 - HALO + r; box column q <-> grid column x0 - HALO + q
     const int gx = x0 - RS_HALO + lane * V;   // grid column of this lane's element 0
+    const int yb = y0 - RS_HALO + warp * RS_RB;  // grid row of the band's first row
 
     if (tid == 0) {
         mbar_init(&bar, 1);
         mbar_init_fence();
-        tmap_prefetch(&tm);
+        tmap_prefetch(&P.tm);
     }
     if (warp == 0) {
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -121,31 +134,50 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
 #endif
-    __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bar, BOX_BYTES);
-        tma_load_3d(box, &tm, x0 - RS_HALO, y0 - RS_HALO, 0, &bar);
-        tma_load_3d(box + RS_BOX_ROWS * RS_W, &tm, x0 - RS_HALO, y0 - RS_HALO + RS_BOX_ROWS, 0, &bar);
-    }
-    const bool ok = mbar_wait_bounded(&bar, 0, timeout_ns);
-    if (!__syncthreads_and(ok)) {
-        // give the copies a bounded chance to land before leaving, then report
-        mbar_wait_bounded(&bar, 0, 1000000ull);
-        if (tid == 0) set_device_error(err, DEV_ERR_TIMEOUT_TMA);
-        return;
-    }
 
-    unsigned colin = 0;  // interior columns among this lane's 4
+    // The points this warp must keep fixed.  Only the boundary ring matters:
+    // points outside the grid (zero-filled rows and columns of the box) may
+    // change freely, since they reach the interior only through the ring,
+    // which never changes.  A band holds at most one ring row (row 0 or R-1)
+    // and a lane at most one ring column (0 or C-1) unless the grid is only
+    // a few rows or one box wide; then the band takes the general path, which
+    // keeps every point outside the interior.
+    const int bx0 = x0 - RS_HALO;  // grid column of box column 0
+    int ncol = 0, fq = -1;         // fq: box column of the ring column in the box
+    if (bx0 <= 0) {
+        ++ncol;
+        fq = -bx0;
+    }
+    if (g.C - 1 - bx0 < RS_W) {
+        ++ncol;
+        fq = g.C - 1 - bx0;
+    }
+    int nrow = 0, frow = -1;  // frow: band row of the ring row in the band
+    if (yb <= 0 && 0 < yb + RS_RB) {
+        ++nrow;
+        frow = -yb;
+    }
+    if (g.R - 1 >= yb && g.R - 1 < yb + RS_RB) {
+        ++nrow;
+        frow = g.R - 1 - yb;
+    }
+    // variant: 0 plain; 1..4 ring column at element variant-1 of lane fq/V;
+    // +5 with a ring row; 10 general.  u0, u1: the ring row's band row and
+    // whether this lane holds the ring column; on the general path the
+    // band's first grid row and this lane's interior-column mask.
+    const int variant =
+        (ncol > 1 || nrow > 1) ? 10 : (ncol == 1 ? fq % V + 1 : 0) + (nrow == 1 ? 5 : 0);
+    int u0 = frow;
+    unsigned u1 = ncol == 1 && lane == fq / V ? 1u : 0u;
+    if (variant == 10) {
+        u0 = yb;
+        u1 = 0;
 #pragma unroll
-    for (int e = 0; e < V; ++e)
-        if (gx + e >= 1 && gx + e <= g.C - 2) colin |= 1u << e;
-    const int yb = y0 - RS_HALO + warp * RS_RB;  // grid row of the band's first row
+        for (int e = 0; e < V; ++e)
+            if (gx + e >= 1 && gx + e <= g.C - 2) u1 |= 1u << e;
+    }
 
     float X[RS_RB][V];
-    rs_static_for<0, RS_RB>([&](auto i_t) {
-        constexpr int i = decltype(i_t)::value;
-        VecIO<ST, V>::load(X[i], box + (warp * RS_RB + i) * RS_W + lane * V);
-    });
     auto put = [&](float *slot, const float (&x)[V]) {
         reinterpret_cast<float4 *>(slot)[lane] = make_float4(x[0], x[1], x[2], x[3]);
     };
@@ -156,16 +188,13 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
         x[2] = v.z;
         x[3] = v.w;
     };
-    put(top[0][warp], X[0]);
-    put(bot[0][warp + 1], X[RS_RB - 1]);
-    __syncthreads();
-
-    const bool edge = x0 - RS_HALO < 1 || x0 - RS_HALO + RS_W > g.C - 1 || y0 - RS_HALO < 1 ||
-                      y0 - RS_HALO + RS_BY > g.R - 1;
     // One step of the band from the edge rows of slot p; the new edge rows go
-    // to slot p ^ 1.
-    auto step = [&](auto edge_t, int p) {
-        constexpr bool EDGE = decltype(edge_t)::value;
+    // to slot p ^ 1.  CF: 0 no ring column, 1 + e ring column at element e
+    // of the lane `fixlane`, -1 the general path; RF: a ring row at band row
+    // `frow`.
+    auto step = [&](auto cf_t, auto rf_t, int p) {
+        constexpr int CF = decltype(cf_t)::value;
+        constexpr bool RF = decltype(rf_t)::value;
         float N[V], S[V];
         get(N, bot[p][warp]);
         get(S, top[p][warp + 1]);
@@ -201,11 +230,21 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
                 o[e] = r.x;
                 o[e + 1] = r.y;
             }
-            if (EDGE) {
-                const bool row_in = yb + i >= 1 && yb + i <= g.R - 2;
+            if constexpr (CF < 0) {
+                const bool row_in = u0 + i >= 1 && u0 + i <= g.R - 2;
 #pragma unroll
                 for (int e = 0; e < V; ++e)
-                    if (!row_in || !((colin >> e) & 1u)) o[e] = X[i][e];
+                    if (!row_in || !((u1 >> e) & 1u)) o[e] = X[i][e];
+            } else {
+                if constexpr (CF > 0) {
+                    if (u1) o[CF - 1] = X[i][CF - 1];
+                }
+                if constexpr (RF) {
+                    if (i == u0) {
+#pragma unroll
+                        for (int e = 0; e < V; ++e) o[e] = X[i][e];
+                    }
+                }
             }
 #pragma unroll
             for (int e = 0; e < V; ++e) X[i][e] = o[e];
@@ -217,12 +256,51 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
         put(top[p ^ 1][warp], X[0]);
         put(bot[p ^ 1][warp + 1], X[RS_RB - 1]);
     };
-    for (int t = 0; t < k; ++t) {
-        if (edge)
-            step(std::true_type(), t & 1);
-        else
-            step(std::false_type(), t & 1);
-        __syncthreads();
+    // all k steps of one variant (the loop is repeated per variant, so that
+    // only that variant's values stay live across it)
+    auto steps = [&](auto cf_t, auto rf_t, int nk) {
+        for (int t = 0; t < nk; ++t) {
+            step(cf_t, rf_t, t & 1);
+            __syncthreads();
+        }
+    };
+    const int k = P.k;
+    ST *const dst = static_cast<ST *>(P.dst);
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar, BOX_BYTES);
+        tma_load_3d(box, &P.tm, x0 - RS_HALO, y0 - RS_HALO, 0, &bar);
+        tma_load_3d(box + RS_BOX_ROWS * RS_W, &P.tm, x0 - RS_HALO, y0 - RS_HALO + RS_BOX_ROWS, 0, &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0, P.timeout_ns);
+    if (!__syncthreads_and(ok)) {
+        // give the copies a bounded chance to land before leaving, then report
+        mbar_wait_bounded(&bar, 0, 1000000ull);
+        if (tid == 0) set_device_error(P.err, DEV_ERR_TIMEOUT_TMA);
+        return;
+    }
+    rs_static_for<0, RS_RB>([&](auto i_t) {
+        constexpr int i = decltype(i_t)::value;
+        VecIO<ST, V>::load(X[i], box + (warp * RS_RB + i) * RS_W + lane * V);
+    });
+    put(top[0][warp], X[0]);
+    put(bot[0][warp + 1], X[RS_RB - 1]);
+    __syncthreads();
+
+    using F = std::false_type;
+    using T = std::true_type;
+    switch (variant) {
+        case 0: steps(std::integral_constant<int, 0>(), F(), k); break;
+        case 1: steps(std::integral_constant<int, 1>(), F(), k); break;
+        case 2: steps(std::integral_constant<int, 2>(), F(), k); break;
+        case 3: steps(std::integral_constant<int, 3>(), F(), k); break;
+        case 4: steps(std::integral_constant<int, 4>(), F(), k); break;
+        case 5: steps(std::integral_constant<int, 0>(), T(), k); break;
+        case 6: steps(std::integral_constant<int, 1>(), T(), k); break;
+        case 7: steps(std::integral_constant<int, 2>(), T(), k); break;
+        case 8: steps(std::integral_constant<int, 3>(), T(), k); break;
+        case 9: steps(std::integral_constant<int, 4>(), T(), k); break;
+        default: steps(std::integral_constant<int, -1>(), F(), k); break;
     }
 
     // write the tile's rows [HALO, HALO + TY) straight from registers
@@ -245,10 +323,11 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
             }
         });
     }
+
 }
 
 // ------------------------------------------------------------------ host -----
-static const void *resident_kernel(int dtype) {
+static const void *resident_fn(int dtype) {
     return dtype == SDFG_BF16 ? reinterpret_cast<const void *>(&resident_pass_kernel<__nv_bfloat16>)
                               : reinterpret_cast<const void *>(&resident_pass_kernel<float>);
 }
@@ -263,6 +342,9 @@ std::vector<int> plan_resident_passes(long long T, int k) {
     return p;
 }
 
+// Runs the passes ks (each k <= 8) from src0, one launch per pass: the first
+// pass writes `first`, then the passes alternate between `second` and
+// `first`; *final receives the buffer the last pass wrote.
 int run_resident_passes(const void *src0, void *first, void *second, const std::vector<int> &ks, int R, int C,
                         int ld, int dtype, DeviceState *st, cudaStream_t s, void **final) {
     *final = const_cast<void *>(src0);
@@ -270,7 +352,7 @@ int run_resident_passes(const void *src0, void *first, void *second, const std::
     if (!resident_supported(dtype)) return set_error(SDFG_ERR_INVAL, "resident kernel: FP32 or BF16 storage only");
     for (int k : ks)
         if (k < 1 || k > RS_HALO) return set_error(SDFG_ERR_INVAL, "resident kernel: k=%d outside 1..%d", k, RS_HALO);
-    const void *fn = resident_kernel(dtype);
+    const void *fn = resident_fn(dtype);
     const size_t smem = static_cast<size_t>(RS_BY) * RS_W * dtype_bytes(dtype);
     static bool attr_done[2] = {false, false};
     const int slot = dtype == SDFG_BF16 ? 1 : 0;
@@ -284,21 +366,23 @@ int run_resident_passes(const void *src0, void *first, void *second, const std::
     if (rc == SDFG_OK) rc = encode_tmap3d(&tm_first, first, dtype, 1, R, C, ld, RS_W, RS_BOX_ROWS);
     if (rc == SDFG_OK) rc = encode_tmap3d(&tm_second, second, dtype, 1, R, C, ld, RS_W, RS_BOX_ROWS);
     if (rc != SDFG_OK) return rc;
-    ResGeo g;
-    g.R = R;
-    g.C = C;
-    g.ld = ld;
-    g.tiles_x = (C + RS_TX - 1) / RS_TX;
-    const unsigned blocks = static_cast<unsigned>(static_cast<long long>(g.tiles_x) * ((R + RS_TY - 1) / RS_TY));
+    ResParams prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.g.R = R;
+    prm.g.C = C;
+    prm.g.ld = ld;
+    prm.g.tiles_x = (C + RS_TX - 1) / RS_TX;
+    prm.g.tiles_y = (R + RS_TY - 1) / RS_TY;
+    prm.err = st->d_err;
+    prm.timeout_ns = test_hooks().timeout_ns ? test_hooks().timeout_ns : DEFAULT_TIMEOUT_NS;
+    const unsigned blocks = static_cast<unsigned>(static_cast<long long>(prm.g.tiles_x) * prm.g.tiles_y);
     const CUtensorMap *tsrc = &tm_src0;
     void *dst = first;
-    int *err = st->d_err;
-    unsigned long long to = DEFAULT_TIMEOUT_NS;
     for (size_t p = 0; p < ks.size(); ++p) {
-        CUtensorMap t = *tsrc;
-        void *dp = dst;
-        int k = ks[p];
-        void *args[] = {&t, &dp, &g, &k, &err, &to};
+        prm.tm = *tsrc;
+        prm.dst = dst;
+        prm.k = ks[p];
+        void *args[] = {&prm};
         TimedLaunch tl = stats_begin(FAM_RESIDENT, s);
 #if SDFG_RESIDENT_PDL
         cudaLaunchConfig_t lc = {};

@@ -59,7 +59,7 @@ def fp32_sequence(g32, T):
     return A
 
 
-SHAPES = [(3, 3), (5, 7), (9, 130), (130, 9), (257, 113), (300, 250), (520, 230), (129, 131)]
+SHAPES = [(3, 3), (5, 7), (9, 130), (130, 9), (257, 113), (300, 250), (520, 230), (129, 131), (140, 236)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -72,6 +72,17 @@ def test_f32_bitwise_sequence_and_oracle(shape, T, k):
     diff = got != want32
     assert not diff.any(), (int(diff.sum()), float(np.abs(got - want32).max()), np.argwhere(diff)[:4].tolist())
     assert np.abs(got.astype(np.float64) - oracle.jacobi2d(h64(x), T, threads=0)).max() <= 1e-4
+
+
+def test_more_tiles_than_sms_bitwise():
+    """2100^2 is 9 x 19 = 171 tiles: more than one wave of CTAs (one per SM),
+    with ring rows and columns at other band rows and lane elements than
+    2048^2 has."""
+    R, C, T = 2100, 2100, 13
+    g = np.random.default_rng(11).random((R, C))
+    x = torch.from_numpy(g).float().cuda()
+    got = run(x, T, 8).cpu().numpy()
+    assert np.array_equal(got, fp32_sequence(x.cpu().numpy(), T))
 
 
 def test_bf16_smooth_field():
