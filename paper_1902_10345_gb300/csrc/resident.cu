@@ -6,11 +6,13 @@
 // (strip, segment) chunk by chunk, so a pass takes as long as one unit's
 // chunks take to stream through the warp.  On a grid that fits in L2 -- the
 // paper's 2048^2 workload -- that per-pass latency, not bandwidth, sets the
-// speed.  Here a CTA of 16 warps loads its box with two TMA copies, each warp
-// takes a band of 17 consecutive box rows into registers, and all bands
-// advance together, one barrier per step, so a pass costs one box load, k
-// steps of arithmetic from registers and one store, and consecutive passes
-// overlap their launch with the previous pass's end.
+// speed.  Here a CTA of 16 warps loads its box with two TMA copies (half a
+// box each, one mbarrier each: warps 0-7 start on the first half while the
+// second lands), each warp takes a band of 17 consecutive box rows into
+// registers, and all bands advance together, one barrier per step, so a pass
+// costs one box load, k steps of arithmetic from registers and the stores,
+// which the last step issues row by row as the rows become final.
+// Consecutive passes overlap their launch with the previous pass's end.
 //
 // Geometry: the box is 272 rows x 128 columns; the tile it updates is the
 // 256 x 112 interior of the box (8 halo rows and columns on each side).  A
@@ -25,8 +27,9 @@
 // each operation rounded on its own (the FP64 oracle's order in FP32).  A
 // row is updated in place: the (n + s) sum of the NEXT row is formed from
 // this row's old values before they are overwritten, so no old copy of a
-// row is kept.  Boundary-ring points and points outside the grid keep their
-// values.  BF16 storage is converted to FP32 at the box load and rounded to
+// row is kept.  Boundary-ring points keep their values; points outside the
+// grid change but are never stored, and reach the interior only through the
+// ring.  BF16 storage is converted to FP32 at the box load and rounded to
 // BF16 (RNE) when the pass stores the tile.
 #include <string.h>
 
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
     constexpr int V = 4;
     constexpr uint32_t BOX_BYTES = RS_BY * RS_W * sizeof(ST);
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar[2];  // one per TMA copy (half box)
     // band-edge rows, double-buffered by step parity: top[p][w] is warp w's
     // first row, bot[p][w + 1] its last; bot[p][0] and top[p][NW] stand for
     // the rows beyond the box (zeros)
@@ -117,7 +120,8 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
     const int yb = y0 - RS_HALO + warp * RS_RB;  // grid row of the band's first row
 
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         mbar_init_fence();
         tmap_prefetch(&P.tm);
     }
@@ -178,6 +182,14 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
     }
 
     float X[RS_RB][V];
+    // Stores: band rows [st_lo, st_hi) lie in the tile and the grid; lanes
+    // whose columns lie in the tile (and the grid) store them, with one
+    // vector store when all V columns are in the grid.
+    ST *const row0 = static_cast<ST *>(P.dst) + static_cast<long long>(yb) * g.ld + gx;
+    const int st_lo = max(0, RS_HALO - warp * RS_RB);
+    const int st_hi = min(min(RS_RB, RS_HALO + RS_TY - warp * RS_RB), g.R - yb);
+    const bool own_cols = lane * V >= RS_HALO && lane * V < RS_HALO + RS_TX && gx < g.C;
+    const bool full_vec = gx + V <= g.C;
     auto put = [&](float *slot, const float (&x)[V]) {
         reinterpret_cast<float4 *>(slot)[lane] = make_float4(x[0], x[1], x[2], x[3]);
     };
@@ -192,9 +204,10 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
     // to slot p ^ 1.  CF: 0 no ring column, 1 + e ring column at element e
     // of the lane `fixlane`, -1 the general path; RF: a ring row at band row
     // `frow`.
-    auto step = [&](auto cf_t, auto rf_t, int p) {
+    auto step = [&](auto cf_t, auto rf_t, auto last_t, int p) {
         constexpr int CF = decltype(cf_t)::value;
         constexpr bool RF = decltype(rf_t)::value;
+        constexpr bool LAST = decltype(last_t)::value;
         float N[V], S[V];
         get(N, bot[p][warp]);
         get(S, top[p][warp + 1]);
@@ -248,44 +261,65 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
             }
 #pragma unroll
             for (int e = 0; e < V; ++e) X[i][e] = o[e];
+            if constexpr (LAST) {
+                // the row is final: store it while the next rows compute
+                if (own_cols && i >= st_lo && i < st_hi) {
+                    ST *q = row0 + static_cast<long long>(i) * g.ld;
+                    if (full_vec) {
+                        VecIO<ST, V>::store(q, X[i]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < V; ++e)
+                            if (gx + e < g.C) q[e] = static_cast<ST>(X[i][e]);
+                    }
+                }
+            }
             if constexpr (i + 1 < RS_RB) {
 #pragma unroll
                 for (int e = 0; e < V; ++e) ns[e] = ns_next[e];
             }
         });
-        put(top[p ^ 1][warp], X[0]);
-        put(bot[p ^ 1][warp + 1], X[RS_RB - 1]);
+        if constexpr (!LAST) {
+            put(top[p ^ 1][warp], X[0]);
+            put(bot[p ^ 1][warp + 1], X[RS_RB - 1]);
+        }
     };
     // all k steps of one variant (the loop is repeated per variant, so that
     // only that variant's values stay live across it)
+    // the last step stores each row of the tile as soon as it is final
     auto steps = [&](auto cf_t, auto rf_t, int nk) {
-        for (int t = 0; t < nk; ++t) {
-            step(cf_t, rf_t, t & 1);
+        for (int t = 0; t < nk - 1; ++t) {
+            step(cf_t, rf_t, std::false_type(), t & 1);
             __syncthreads();
         }
+        step(cf_t, rf_t, std::true_type(), (nk - 1) & 1);
     };
     const int k = P.k;
-    ST *const dst = static_cast<ST *>(P.dst);
     __syncthreads();
     if (tid == 0) {
-        mbar_arrive_expect_tx(&bar, BOX_BYTES);
-        tma_load_3d(box, &P.tm, x0 - RS_HALO, y0 - RS_HALO, 0, &bar);
-        tma_load_3d(box + RS_BOX_ROWS * RS_W, &P.tm, x0 - RS_HALO, y0 - RS_HALO + RS_BOX_ROWS, 0, &bar);
+        // two half boxes of 136 rows: warps 0-7 own the first, 8-15 the second
+        mbar_arrive_expect_tx(&bar[0], BOX_BYTES / 2);
+        tma_load_3d(box, &P.tm, x0 - RS_HALO, y0 - RS_HALO, 0, &bar[0]);
+        mbar_arrive_expect_tx(&bar[1], BOX_BYTES / 2);
+        tma_load_3d(box + RS_BOX_ROWS * RS_W, &P.tm, x0 - RS_HALO, y0 - RS_HALO + RS_BOX_ROWS, 0, &bar[1]);
     }
-    const bool ok = mbar_wait_bounded(&bar, 0, P.timeout_ns);
-    if (!__syncthreads_and(ok)) {
-        // give the copies a bounded chance to land before leaving, then report
-        mbar_wait_bounded(&bar, 0, 1000000ull);
-        if (tid == 0) set_device_error(P.err, DEV_ERR_TIMEOUT_TMA);
-        return;
-    }
+    static_assert(RS_BOX_ROWS == (RS_NW / 2) * RS_RB, "each half box holds the bands of half the warps");
+    const bool ok = mbar_wait_bounded(&bar[warp < RS_NW / 2 ? 0 : 1], 0, P.timeout_ns);
+    // (a warp whose wait ran out reads stale shared memory here; the check
+    // below then ends the CTA before any value is used)
     rs_static_for<0, RS_RB>([&](auto i_t) {
         constexpr int i = decltype(i_t)::value;
         VecIO<ST, V>::load(X[i], box + (warp * RS_RB + i) * RS_W + lane * V);
     });
     put(top[0][warp], X[0]);
     put(bot[0][warp + 1], X[RS_RB - 1]);
-    __syncthreads();
+    if (!__syncthreads_and(ok)) {
+        // give the copies a bounded chance to land before leaving, then report
+        mbar_wait_bounded(&bar[0], 0, 1000000ull);
+        mbar_wait_bounded(&bar[1], 0, 1000000ull);
+        if (tid == 0) set_device_error(P.err, DEV_ERR_TIMEOUT_TMA);
+        return;
+    }
 
     using F = std::false_type;
     using T = std::true_type;
@@ -301,27 +335,6 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
         case 8: steps(std::integral_constant<int, 3>(), T(), k); break;
         case 9: steps(std::integral_constant<int, 4>(), T(), k); break;
         default: steps(std::integral_constant<int, -1>(), F(), k); break;
-    }
-
-    // write the tile's rows [HALO, HALO + TY) straight from registers
-    const bool own_cols = lane * V >= RS_HALO && lane * V < RS_HALO + RS_TX && gx < g.C;
-    if (own_cols) {
-        const bool full_vec = gx + V <= g.C;
-        rs_static_for<0, RS_RB>([&](auto i_t) {
-            constexpr int i = decltype(i_t)::value;
-            const int r = warp * RS_RB + i;
-            const int y = yb + i;
-            if (r >= RS_HALO && r < RS_HALO + RS_TY && y < g.R) {
-                ST *q = dst + static_cast<long long>(y) * g.ld + gx;
-                if (full_vec) {
-                    VecIO<ST, V>::store(q, X[i]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < V; ++e)
-                        if (gx + e < g.C) q[e] = static_cast<ST>(X[i][e]);
-                }
-            }
-        });
     }
 
 }
