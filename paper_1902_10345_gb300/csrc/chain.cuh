@@ -11,6 +11,10 @@
 
 namespace sdfg {
 
+#ifndef SDFG_CHAIN_TURN
+#define SDFG_CHAIN_TURN 6  // rows per turn of a chain's chunk loop (4 on the persistent units)
+#endif
+
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // Spin (lane-parallel) until every lane's predicate holds; false on timeout.
@@ -69,6 +73,7 @@ static __device__ __noinline__ int chain_wait_rows(const int *prog_prev, int bet
 // load, publishes this chain's progress after its chunks.
 struct ChainHook {
     static constexpr bool EDGES = true;
+    static constexpr int TURN = SDFG_CHAIN_TURN;
     const int *prog_prev;  // counters of pass p-1 (nullptr for pass 0: the input is ready)
     int *prog_own;         // this chain's counter
     int beta_prev, jmin_prev, L, R, n_strips, s, lane;

@@ -251,7 +251,7 @@ __device__ __noinline__ inline bool drain_after_timeout(uint64_t *bars, uint32_t
 #define SDFG_RES_FP64 0  // residual: square and sum every difference in FP64 (else FP32 groups)
 #endif
 #ifndef SDFG_RING2_TURN
-#define SDFG_RING2_TURN 4  // rows per turn of the two-row-ring chunk loop
+#define SDFG_RING2_TURN 4  // rows per turn of the two-row-ring chunk loop (per-pass and persistent units)
 #endif
 static_assert(CHUNK_ROWS % SDFG_RING2_TURN == 0, "chunks are whole turns");
 
@@ -260,9 +260,12 @@ static_assert(CHUNK_ROWS % SDFG_RING2_TURN == 0, "chunks are whole turns");
 // chunk c is loaded (false: a bounded wait ran out) and done(c) once chunk c's
 // rows are stored and the warp is synchronised.  EDGES: a unit of the
 // reassociated pipe may hold row 0 or row R-1 (see step2).  The units of the
-// per-pass and persistent kernels need none of it.
+// per-pass and persistent kernels need none of it.  TURN: rows per turn of
+// the two-row-ring chunk loop (one unrolled body); the best value differs
+// between the kernels (measured).
 struct NoHook {
     static constexpr bool EDGES = false;
+    static constexpr int TURN = SDFG_RING2_TURN;
     __device__ __forceinline__ bool ready(int) { return true; }
     __device__ __forceinline__ void done(int) {}
 };
@@ -521,9 +524,9 @@ struct UnitPipe {
         }
     }
 
-    template <bool EDGE>
+    template <bool EDGE, int TURN>
     __device__ __forceinline__ void chunk_body2(int r0, const ST *src, ST *out) {
-        constexpr int TURN = SDFG_RING2_TURN;
+        static_assert(CHUNK_ROWS % TURN == 0, "chunks are whole turns");
         const size_t ldr = static_cast<size_t>(ld);
 #pragma unroll 1
         for (int h = 0; h < CHUNK_ROWS / TURN; ++h) {
@@ -609,9 +612,9 @@ struct UnitPipe {
                 // a centre row of some level may be row 0 or row R-1
                 const bool edge = Hook::EDGES && (r0 <= K || (r0 + CHUNK_ROWS - 2 >= R - 1 && r0 - K <= R - 1));
                 if (edge)
-                    chunk_body2<true>(r0, src, out);
+                    chunk_body2<true, Hook::TURN>(r0, src, out);
                 else
-                    chunk_body2<false>(r0, src, out);
+                    chunk_body2<false, Hook::TURN>(r0, src, out);
             } else if (fast && !ONE_BODY) {
                 chunk_body<false>(r0, src, out);
             } else {
