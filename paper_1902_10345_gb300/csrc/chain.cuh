@@ -70,10 +70,12 @@ static __device__ __noinline__ int chain_wait_rows(const int *prog_prev, int bet
 }
 
 // UnitPipe hook of one chain: waits on pass p-1's progress before each chunk
-// load, publishes this chain's progress after its chunks.
+// load (chunks of CR rows), publishes this chain's progress after its chunks.
+template <int CR>
 struct ChainHook {
     static constexpr bool EDGES = true;
     static constexpr int TURN = SDFG_CHAIN_TURN;
+    static constexpr int ROWS = CR;
     const int *prog_prev;  // counters of pass p-1 (nullptr for pass 0: the input is ready)
     int *prog_own;         // this chain's counter
     int beta_prev, jmin_prev, L, R, n_strips, s, lane;
@@ -86,8 +88,8 @@ struct ChainHook {
     // stored in the three strips around s.
     __device__ __forceinline__ bool ready(int c) {
         if (!prog_prev) return true;
-        const int r0 = rb + c * CHUNK_ROWS;
-        const int need_hi = min(R - 1, r0 + CHUNK_ROWS - 1 + extra);
+        const int r0 = rb + c * CR;
+        const int need_hi = min(R - 1, r0 + CR - 1 + extra);
         if (need_hi <= ok_hi) return true;
         ok_hi = chain_wait_rows(prog_prev, beta_prev, jmin_prev, L, R, n_strips, s, ok_hi + 1, need_hi, err,
                                 timeout_ns);
@@ -98,23 +100,24 @@ struct ChainHook {
     // `pub` chunks and at the end.
     __device__ __forceinline__ void done(int c) {
         if (c != n_chunks - 1 && (c + 1) % pub != 0) return;
-        const int r0 = rb + c * CHUNK_ROWS;
-        const int v = max(0, min(r0 + CHUNK_ROWS - K, y1) - y0);
+        const int r0 = rb + c * CR;
+        const int v = max(0, min(r0 + CR - K, y1) - y0);
         if (lane == 0) st_release_gpu(prog_own, v);
     }
 };
 
 // One chain: output rows [lo, hi) of strip s, read through `tmap`, written to dst.
-template <class ST, int V, int K>
+template <class ST, int V, int K, class Hook>
 __device__ __forceinline__ bool run_chain(const void *tmap, ST *dst, const GridGeo &g, int s, int lo, int hi,
-                                          ST *ring, uint64_t *bars, uint32_t &chunk_ctr, ChainHook &hk,
+                                          ST *ring, uint64_t *bars, uint32_t &chunk_ctr, Hook &hk,
                                           unsigned long long timeout_ns) {
+    constexpr int CR = Hook::ROWS;
     constexpr int W = 32 * V;
     const int lane = threadIdx.x & 31;
     const int X = s * g.wout - g.h;
     const int rb = max(0, lo - K);
     const int n_steps = hi + K - rb;
-    const int n_chunks = (n_steps + CHUNK_ROWS - 1) / CHUNK_ROWS;
+    const int n_chunks = (n_steps + CR - 1) / CR;
     const int gc0 = X + lane * V;
     const int hl = g.h / V;
     unsigned colmask = 0;
@@ -139,7 +142,7 @@ __device__ __forceinline__ bool run_chain(const void *tmap, ST *dst, const GridG
     bool ok;
 #define SDFG_CHAIN_PIPE(CHK, EX, SY0, SY1)                                                              \
     {                                                                                                   \
-        UnitPipe<ST, V, K, CHK, false, EX> p;                                                           \
+        UnitPipe<ST, V, K, CHK, false, EX, CR> p;                                                       \
         p.tmap = tmap; p.dst = dst; p.ld = g.ld; p.R = g.R; p.C = g.C;                                  \
         p.X = X; p.y0 = lo; p.y1 = hi; p.rb = rb; p.n_steps = n_steps; p.n_chunks = n_chunks;           \
         p.sy0 = (SY0); p.sy1 = (SY1);                                                                   \
@@ -152,7 +155,7 @@ __device__ __forceinline__ bool run_chain(const void *tmap, ST *dst, const GridG
     // (rows 0 and R-1, and on a boundary strip columns 0 and C-1); it never
     // stores them, the caller's ring copy provides them.  FP64 keeps the
     // exact order everywhere and stores the ring itself.
-    constexpr bool SCALED_OK = UnitPipe<ST, V, K, false, false, false>::RING2;
+    constexpr bool SCALED_OK = UnitPipe<ST, V, K, false, false, false, CR>::RING2;
     if (!SCALED_OK) {
         if (colchk)
             SDFG_CHAIN_PIPE(true, true, lo, hi)
@@ -168,19 +171,16 @@ __device__ __forceinline__ bool run_chain(const void *tmap, ST *dst, const GridG
     return ok;
 }
 
-template <class ST, int V>
+template <class ST, int V, class Hook>
 __device__ __forceinline__ bool chain_depth(int k, const void *tmap, ST *dst, const GridGeo &g, int s, int lo, int hi,
-                                            ST *ring, uint64_t *bars, uint32_t &ctr, ChainHook &hk,
+                                            ST *ring, uint64_t *bars, uint32_t &ctr, Hook &hk,
                                             unsigned long long timeout_ns) {
     switch (k) {
-        case 1: return run_chain<ST, V, 1>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
-        case 2: return run_chain<ST, V, 2>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
-        case 4: return run_chain<ST, V, 4>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
-        default: return run_chain<ST, V, 8>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
+        case 1: return run_chain<ST, V, 1, Hook>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
+        case 2: return run_chain<ST, V, 2, Hook>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
+        case 4: return run_chain<ST, V, 4, Hook>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
+        default: return run_chain<ST, V, 8, Hook>(tmap, dst, g, s, lo, hi, ring, bars, ctr, hk, timeout_ns);
     }
 }
 
-#ifndef SDFG_CHAIN_PUB
-#define SDFG_CHAIN_PUB 12  // chunks between two progress updates of a chain
-#endif
 }  // namespace sdfg

@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(128, SDFG_CK_MINB) chain_batch_kernel(const CB
         mbar_init_fence();
     }
     __syncwarp();
-    ST *ring = reinterpret_cast<ST *>(smem_raw) + static_cast<size_t>(warp) * STAGES * CHUNK_ROWS * 32 * V;
+    constexpr int CR = chain_chunk_rows(sizeof(ST));
+    ST *ring = reinterpret_cast<ST *>(smem_raw) + static_cast<size_t>(warp) * STAGES * CR * 32 * V;
     uint32_t ctr = 0;
     while (true) {
         int item = 0;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(128, SDFG_CK_MINB) chain_batch_kernel(const CB
         const int ns = geo.n_strips;
         const int po = G.pass_off;
         const int k = __ldg(P.pass_k + po + p);
-        ChainHook hk;
+        ChainHook<CR> hk;
         hk.prog_prev = p > 0 ? P.prog + __ldg(P.prog_off + po + p - 1) : nullptr;
         hk.beta_prev = p > 0 ? __ldg(P.pass_beta + po + p - 1) : 0;
         hk.jmin_prev = p > 0 ? __ldg(P.pass_jmin + po + p - 1) : 0;
@@ -206,7 +207,7 @@ int ChainBatch::build(const std::vector<GridRun> &runs, cudaStream_t s) {
     const int S = dtype_bytes(dtype);
     const int W = 32 * lane_cols(S);
     const int Lc = L > 0 ? std::max(L, 4 * k) : 512;
-    const int pb = pub > 0 ? pub : SDFG_CHAIN_PUB;
+    const int pb = pub > 0 ? pub : chain_pub_chunks(dtype_bytes(dtype));
     auto fdiv = [](long long a, long long b) { return static_cast<int>(a >= 0 ? a / b : -((-a + b - 1) / b)); };
     std::vector<CGrid> grids(n);
     std::vector<int> pk, pbeta, pjmin, pjmax, poff, P(n);
@@ -233,7 +234,7 @@ int ChainBatch::build(const std::vector<GridRun> &runs, cudaStream_t s) {
             if (r.tmaps) {
                 G.tm[b] = r.tmaps[b];
             } else {
-                int rc = encode_tmap(&G.tm[b], r.buf[b], dtype, r.R, r.C, r.ld, W);
+                int rc = encode_tmap(&G.tm[b], r.buf[b], dtype, r.R, r.C, r.ld, W, chain_chunk_rows(dtype_bytes(dtype)));
                 if (rc != SDFG_OK) return rc;
             }
         }
@@ -347,7 +348,7 @@ int ChainBatch::build(const std::vector<GridRun> &runs, cudaStream_t s) {
     ring = base + o_ring;
     // CTAs: every SM full, or fewer when there are fewer items than warps
     const void *fn = chain_batch_fn(dtype);
-    const size_t smem = temporal_smem_bytes(dtype, 4);
+    const size_t smem = chain_smem_bytes(dtype, 4);
     SDFG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int bps = 0;
     SDFG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 128, smem));
@@ -372,7 +373,7 @@ int ChainBatch::enqueue(DeviceState *st, cudaStream_t s) {
     void *args[] = {&prm};
     TimedLaunch t = stats_begin(FAM_SKEWED, s);
     cudaError_t e = cudaLaunchKernel(chain_batch_fn(dtype), dim3(blocks), dim3(128), args,
-                                     temporal_smem_bytes(dtype, 4), s);
+                                     chain_smem_bytes(dtype, 4), s);
     stats_end(t, s);
     if (e != cudaSuccess) return cuda_error(e, "chain batch launch");
     return SDFG_OK;

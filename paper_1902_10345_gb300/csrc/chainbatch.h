@@ -29,6 +29,13 @@ struct GridCopy {
     int rows, cols, ld_src, ld_dst;
 };
 
+// Shared memory of a chain-kernel CTA of `warps` warps: each warp's TMA ring
+// of STAGES chunks of chain_chunk_rows rows.
+inline size_t chain_smem_bytes(int dtype, int warps) {
+    const int S = dtype_bytes(dtype);
+    return static_cast<size_t>(warps) * STAGES * chain_chunk_rows(S) * 32 * lane_cols(S) * S;
+}
+
 // Copies n ring descriptors / grid descriptors that live in device memory.
 int launch_ring_copy(const RingCopy *d_descs, int n, int max_ring, int dtype, cudaStream_t s);
 int launch_grid_copy(const GridCopy *d_descs, int n, int max_rows, int dtype, cudaStream_t s);

@@ -12,6 +12,34 @@ namespace sdfg {
 constexpr int CHUNK_ROWS = SDFG_CHUNK_ROWS;  // rows per TMA box (a multiple of the 3-row register rotation)
 constexpr int STAGES = SDFG_STAGES;          // TMA ring depth per warp
 static_assert(CHUNK_ROWS % 3 == 0, "chunks are whole turns of the 3-row rotation");
+
+// The chain kernels (skewed.cu, chain_batch.cu) stream taller chunks: 18
+// rows for 4- and 8-byte storage (three CTAs' TMA rings still fit in an SM's
+// shared memory), 24 for 2-byte storage (measured best for each).  Their
+// progress is published every ~144 rows.
+#ifndef SDFG_CHAIN_CHUNK_ROWS_4
+#define SDFG_CHAIN_CHUNK_ROWS_4 18
+#endif
+#ifndef SDFG_CHAIN_CHUNK_ROWS_2
+#define SDFG_CHAIN_CHUNK_ROWS_2 24
+#endif
+#ifndef SDFG_CHAIN_PUB_ROWS
+#define SDFG_CHAIN_PUB_ROWS 144
+#endif
+#ifdef __CUDACC__
+#define SDFG_HD __host__ __device__
+#else
+#define SDFG_HD
+#endif
+SDFG_HD constexpr int chain_chunk_rows(int elem_bytes) {
+    return elem_bytes == 2 ? SDFG_CHAIN_CHUNK_ROWS_2 : SDFG_CHAIN_CHUNK_ROWS_4;
+}
+// default chunks between two progress updates of a chain
+SDFG_HD constexpr int chain_pub_chunks(int elem_bytes) {
+    return SDFG_CHAIN_PUB_ROWS / chain_chunk_rows(elem_bytes) > 0 ? SDFG_CHAIN_PUB_ROWS / chain_chunk_rows(elem_bytes)
+                                                                  : 1;
+}
+static_assert(chain_chunk_rows(2) % 6 == 0 && chain_chunk_rows(4) % 6 == 0, "chain chunks are whole 6-row turns");
 constexpr int MAX_WARPS = 16;  // warps per CTA upper bound
 
 // Codes a kernel writes to the per-device error word (first writer wins).

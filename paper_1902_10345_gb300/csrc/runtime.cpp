@@ -85,7 +85,7 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols, int ld, int box_cols) {
+int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols, int ld, int box_cols, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return set_error(SDFG_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const CUtensorMapDataType t = dtype == SDFG_F64    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
@@ -93,7 +93,7 @@ int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols
                                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
     const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * dtype_bytes(dtype)};
-    const cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(CHUNK_ROWS)};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(tm, t, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

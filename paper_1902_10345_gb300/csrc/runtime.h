@@ -44,9 +44,10 @@ inline bool dtype_valid(int dt) { return dt == SDFG_F32 || dt == SDFG_BF16 || dt
 inline int dtype_bytes(int dt) { return dt == SDFG_F64 ? 8 : (dt == SDFG_BF16 ? 2 : 4); }
 
 // ---- TMA ---------------------------------------------------------------------
-// 2-D tensor map over a rows x cols grid with pitch ld; box = box_cols x CHUNK_ROWS;
-// out-of-range elements read as zero.
-int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols, int ld, int box_cols);
+// 2-D tensor map over a rows x cols grid with pitch ld; box = box_cols x
+// box_rows (CHUNK_ROWS by default); out-of-range elements read as zero.
+int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols, int ld, int box_cols,
+                int box_rows = CHUNK_ROWS);
 // Rank-3 map over a depth x rows x cols box (row pitch ld elements, plane
 // pitch rows*ld): boxes of box_cols x box_rows x 1.
 int encode_tmap3d(CUtensorMap *tm, const void *base, int dtype, int depth, int rows, int cols, int ld, int box_cols,

@@ -21,9 +21,9 @@
 // the end, how many of its chain's rows are stored: a release store after a
 // warp barrier.  The release waits for the warp's stores in flight, about a
 // microsecond under full HBM traffic, so publishing after every chunk costs
-// ~13% and every 12 chunks ~2%, while a longer interval adds lag from pass to
-// pass (12 chunks and 512-row chains are the measured best on 8192^2).
-// Before loading input rows [r0, r0 + CHUNK_ROWS) a warp waits (bounded,
+// ~13% and every ~144 rows ~2%, while a longer interval adds lag from pass
+// to pass (~144 rows and 512-row chains are the measured best on 8192^2).
+// Before loading input rows [r0, r0 + CR) a warp waits (bounded,
 // acquire loads) until pass p-1 has stored those rows, plus
 // e = max(0, k_{p-1} - k_p) more, in strips s-1, s, s+1 (the first wait
 // starts e rows above the chain's first input row).  That also orders every
@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(128, SDFG_CK_MINB) chain_kernel(const __grid_c
                 if (P.buf[b]) tmap_prefetch(&P.tm[b]);
     }
     __syncwarp();
-    ST *ring = reinterpret_cast<ST *>(smem_raw) + static_cast<size_t>(warp) * STAGES * CHUNK_ROWS * 32 * V;
+    constexpr int CR = chain_chunk_rows(sizeof(ST));
+    ST *ring = reinterpret_cast<ST *>(smem_raw) + static_cast<size_t>(warp) * STAGES * CR * 32 * V;
     uint32_t ctr = 0;
     const GridGeo geo = P.geo;
     const int ns = geo.n_strips;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(128, SDFG_CK_MINB) chain_kernel(const __grid_c
         const int4 b = __ldg(P.blocks + blk);
         const int p = b.x, j = b.y, lo = b.z, hi = b.w;
         const int k = __ldg(P.pass_k + p);
-        ChainHook hk;
+        ChainHook<CR> hk;
         hk.prog_prev = p > 0 ? P.prog + __ldg(P.prog_off + p - 1) : nullptr;
         hk.beta_prev = p > 0 ? __ldg(P.pass_beta + p - 1) : 0;
         hk.jmin_prev = p > 0 ? __ldg(P.pass_jmin + p - 1) : 0;
@@ -255,7 +256,7 @@ int chain_plan_build(ChainPlan *c, DeviceState *st, cudaStream_t s) {
     q.buf[2] = c->in == c->out ? nullptr : const_cast<void *>(c->in);
     for (int b = 0; b < 3; ++b)
         if (q.buf[b]) {
-            rc = encode_tmap(&q.tm[b], q.buf[b], c->dtype, R, c->C, c->ld, W);
+            rc = encode_tmap(&q.tm[b], q.buf[b], c->dtype, R, c->C, c->ld, W, chain_chunk_rows(S));
             if (rc != SDFG_OK) return rc;
         }
     q.geo = g;
@@ -279,7 +280,7 @@ int chain_plan_build(ChainPlan *c, DeviceState *st, cudaStream_t s) {
         q.first_dst = (P % 2 == 1) ? 0 : 1;
     }
     c->last = q.first_dst ^ ((P - 1) & 1);
-    const size_t smem = temporal_smem_bytes(c->dtype, 4);
+    const size_t smem = chain_smem_bytes(c->dtype, 4);
     int bps = 0;
     rc = chain_blocks_per_sm(c->dtype, 4, smem);
     if (rc < 0) return rc;
@@ -292,12 +293,12 @@ int chain_plan_build(ChainPlan *c, DeviceState *st, cudaStream_t s) {
 
 // The chain kernel's pass plan for T steps at depth k: plan_passes(T, k).
 // L: chain length in rows (0 = 512); pub: chunks between progress updates
-// (0 = SDFG_CHAIN_PUB).  FP32, BF16 and FP64 storage; in/out must be
+// (0 = about every 144 rows).  FP32, BF16 and FP64 storage; in/out must be
 // TMA-compatible.
 int run_single_chain(const void *in, void *out, int R, int C, int ld, long long T, int dtype, int k, int L, int pub,
                      DeviceState *st, cudaStream_t s) {
     if (L <= 0) L = 512;
-    if (pub <= 0) pub = SDFG_CHAIN_PUB;
+    if (pub <= 0) pub = chain_pub_chunks(dtype_bytes(dtype));
     L = std::max(L, 4 * k);
     std::lock_guard<std::mutex> lk(g_chain_mu);
     ChainPlan *c = nullptr;
@@ -343,7 +344,7 @@ int run_single_chain(const void *in, void *out, int R, int C, int ld, long long 
     ChainParams prm = c->prm;
     prm.timeout_ns = test_hooks().timeout_ns ? test_hooks().timeout_ns : DEFAULT_TIMEOUT_NS;
     void *args[] = {&prm};
-    const size_t smem = temporal_smem_bytes(dtype, 4);
+    const size_t smem = chain_smem_bytes(dtype, 4);
     TimedLaunch t = stats_begin(FAM_SKEWED, s);
     cudaError_t e = cudaLaunchKernel(chain_fn(dtype), dim3(c->blocks), dim3(128), args, smem, s);
     stats_end(t, s);

@@ -270,8 +270,10 @@ struct NoHook {
     __device__ __forceinline__ void done(int) {}
 };
 
-template <class ST, int V, int K, bool COLCHK, bool RES, bool EXACT>
+// CR: rows per TMA chunk (CHUNK_ROWS; the chain kernels stream taller ones).
+template <class ST, int V, int K, bool COLCHK, bool RES, bool EXACT, int CR = CHUNK_ROWS>
 struct UnitPipe {
+    static_assert(CR % 3 == 0, "chunks are whole turns of the 3-row rotation");
     using CT = typename Store<ST>::CT;
     // inner levels pack the column pairs (0, 2), (1, 3); BF16 rows (the
     // 2-byte type) enter registers through a conversion that can place them
@@ -280,7 +282,7 @@ struct UnitPipe {
     static constexpr int PAIRS0 = !SPLIT ? PAIRS_NATURAL : sizeof(ST) == 2 ? PAIRS_SPLIT : PAIRS_ENTRY;
     static constexpr int PAIRS1 = SPLIT ? PAIRS_SPLIT : PAIRS_NATURAL;
     static constexpr int W = 32 * V;
-    static constexpr uint32_t CHUNK_BYTES = CHUNK_ROWS * W * sizeof(ST);
+    static constexpr uint32_t CHUNK_BYTES = CR * W * sizeof(ST);
     // units away from the boundary ring reassociate (see level_sum); a unit
     // that holds a boundary row or column keeps the exact order throughout
     static constexpr bool SCALED = sizeof(CT) == 4 && !EXACT;
@@ -303,7 +305,7 @@ struct UnitPipe {
     unsigned colmask, resmask;
     bool own_lane, full_vec;
     int res_flags;
-    // group sums (at most CHUNK_ROWS rows of one lane's V columns): in the
+    // group sums (at most CR rows of one lane's V columns): in the
     // storage type's arithmetic, or (SDFG_RES_FP64) every square in FP64
     using RT = typename std::conditional<SDFG_RES_FP64 != 0, double, CT>::type;
     RT g_ref, g_chk;
@@ -313,7 +315,7 @@ struct UnitPipe {
     __device__ __forceinline__ void issue(int c) {
         const uint32_t slot = (base + static_cast<uint32_t>(c)) % STAGES;
         mbar_arrive_expect_tx(&bars[slot], CHUNK_BYTES);
-        tma_load_2d(ring + slot * (CHUNK_ROWS * W), tmap, X, rb + c * CHUNK_ROWS, &bars[slot]);
+        tma_load_2d(ring + slot * (CR * W), tmap, X, rb + c * CR, &bars[slot]);
     }
 
     __device__ __forceinline__ void accumulate(RT &g, const CT (&o)[V], const CT (&c)[V]) {
@@ -526,10 +528,10 @@ struct UnitPipe {
 
     template <bool EDGE, int TURN>
     __device__ __forceinline__ void chunk_body2(int r0, const ST *src, ST *out) {
-        static_assert(CHUNK_ROWS % TURN == 0, "chunks are whole turns");
+        static_assert(CR % TURN == 0, "chunks are whole turns");
         const size_t ldr = static_cast<size_t>(ld);
 #pragma unroll 1
-        for (int h = 0; h < CHUNK_ROWS / TURN; ++h) {
+        for (int h = 0; h < CR / TURN; ++h) {
 #pragma unroll
             for (int i = 0; i < TURN; ++i) step2<EDGE>(r0 + i, src + i * W, out + i * ldr);
             r0 += TURN;
@@ -539,13 +541,13 @@ struct UnitPipe {
     }
 
     // `out` points at output row r0-K (it is only dereferenced for rows the
-    // unit owns).  The chunk is CHUNK_ROWS/3 turns of one 3-row body: a
+    // unit owns).  The chunk is CR/3 turns of one 3-row body: a
     // small hot loop (instruction cache).
     template <bool SLOW>
     __device__ __forceinline__ void chunk_body(int r0, const ST *src, ST *out) {
         const size_t ldr = static_cast<size_t>(ld);
 #pragma unroll 1
-        for (int h = 0; h < CHUNK_ROWS / 3; ++h) {
+        for (int h = 0; h < CR / 3; ++h) {
             step<0, SLOW>(r0 + 0, src + 0 * W, out);
             step<1, SLOW>(r0 + 1, src + 1 * W, out + ldr);
             step<2, SLOW>(r0 + 2, src + 2 * W, out + 2 * ldr);
@@ -595,12 +597,12 @@ struct UnitPipe {
             // made warp-uniform so no lane is left behind in a shuffle
             const bool ok = mbar_wait_bounded(&bars[slot], (g / STAGES) & 1u, timeout_ns);
             if (!__all_sync(FULL_MASK, ok)) return drain_after_timeout(bars, base, issued, c);
-            const int r0 = rb + c * CHUNK_ROWS;
-            const ST *src = ring + slot * (CHUNK_ROWS * W) + lane * V;
+            const int r0 = rb + c * CR;
+            const ST *src = ring + slot * (CR * W) + lane * V;
             // Rows past the unit's last step are in the box (zero-filled past
             // the grid) and only produce rows that are never stored.
-            const bool fast = (r0 >= K + 1) && (r0 + CHUNK_ROWS <= R) && (r0 - K >= y0) &&
-                              (r0 + CHUNK_ROWS - K <= y1);
+            const bool fast = (r0 >= K + 1) && (r0 + CR <= R) && (r0 - K >= y0) &&
+                              (r0 + CR - K <= y1);
             // pointer arithmetic only: rows before 0 are never dereferenced
             ST *out = dst + (static_cast<ptrdiff_t>(r0) - K) * ld + (X + lane * V);
             // A reassociated unit's boundary-checked body differs from the fast
@@ -610,7 +612,7 @@ struct UnitPipe {
             constexpr bool ONE_BODY = SDFG_SCALED_ONE_BODY && sizeof(CT) == 4 && !EXACT;
             if constexpr (RING2) {
                 // a centre row of some level may be row 0 or row R-1
-                const bool edge = Hook::EDGES && (r0 <= K || (r0 + CHUNK_ROWS - 2 >= R - 1 && r0 - K <= R - 1));
+                const bool edge = Hook::EDGES && (r0 <= K || (r0 + CR - 2 >= R - 1 && r0 - K <= R - 1));
                 if (edge)
                     chunk_body2<true, Hook::TURN>(r0, src, out);
                 else
