@@ -10,6 +10,7 @@ import concurrent.futures as cf
 import glob
 import hashlib
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -65,17 +66,27 @@ KERNEL_FILES_RESIDENT = ["device_common.cuh", "resident.cu"]
 KERNEL_FILES_CHAIN = ["device_common.cuh", "temporal_unit.cuh", "geometry.h", "chain.cuh", "skewed.cu", "chain_batch.cu"]
 
 
+_TOKENS = re.compile(r'"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'|//[^\n]*|/\*.*?\*/', re.S)
+
+
+def _code_only(text: str) -> str:
+    """C/C++/CUDA source without comments and with whitespace runs collapsed
+    (string and character literals, such as inline PTX, are kept)."""
+    text = _TOKENS.sub(lambda m: " " if m.group(0).startswith("/") else m.group(0), text)
+    return " ".join(text.split())
+
+
 def kernel_digest(files=None) -> str:
     """Digest of the device sources and flags that define the kernels (used
     to tell whether a committed profile still describes the current kernels);
-    files: the 2-D kernels' sources by default, KERNEL_FILES_3D,
-    KERNEL_FILES_SOR, KERNEL_FILES_RESIDENT or KERNEL_FILES_CHAIN for the
-    3-D, SOR, register-resident and chain kernels."""
+    comments and layout do not count.  files: the 2-D kernels' sources by
+    default, KERNEL_FILES_3D, KERNEL_FILES_SOR, KERNEL_FILES_RESIDENT or
+    KERNEL_FILES_CHAIN for the 3-D, SOR, register-resident and chain kernels."""
     h = hashlib.sha256()
     for f in files or KERNEL_FILES:
-        with open(os.path.join(CSRC, f), "rb") as fh:
+        with open(os.path.join(CSRC, f), encoding="utf-8") as fh:
             h.update(f.encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     h.update(" ".join(NVCC_FLAGS).encode())
     return h.hexdigest()[:16]
 

@@ -232,12 +232,13 @@ __device__ __noinline__ inline bool drain_after_timeout(uint64_t *bars, uint32_t
 }
 
 // ---------------------------------------------------------- the unit pipe --
-// Rows are consumed in chunks of CHUNK_ROWS (6 = two turns of the 3-slot
-// register rotation), so one chunk is one straight-line block: all of its
-// levels and rows can be interleaved by the compiler (level l of row i+1 only
-// depends on level l-1 of rows i-1..i+1).  Chunks away from the grid's top and
-// bottom rows and inside the unit's output rows take the FAST body, with no
-// boundary or range test at all.
+// Rows are consumed in chunks of CR rows (one TMA box: CHUNK_ROWS = 12 for
+// the per-pass and persistent kernels, 18 or 24 for the chain kernels), each
+// chunk a few turns of one unrolled body of rows: within a body all levels
+// and rows can be interleaved by the compiler (level l of row i+1 only
+// depends on level l-1 of rows i-1..i+1).  The exact-order pipe's chunks away
+// from the grid's top and bottom rows and inside the unit's output rows take
+// a FAST body, with no boundary or range test at all.
 #ifndef SDFG_SCALED_ONE_BODY
 #define SDFG_SCALED_ONE_BODY 1
 #endif

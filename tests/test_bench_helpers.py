@@ -53,6 +53,17 @@ def test_committed_traffic_lookup():
         assert bench.committed_traffic(digest, workload + "_other") is None, name
 
 
+def test_kernel_digest_ignores_comments_and_layout_only():
+    from paper_1902_10345_gb300 import build
+
+    code = 'int a = 1; // one\n/* two\n lines */ asm("add.rn.f32x2 d, a, b; // kept");\nchar c = \'/\';'
+    bare = 'int a = 1;\n asm("add.rn.f32x2 d, a, b; // kept");   char c = \'/\';'
+    assert build._code_only(code) == build._code_only(bare)
+    assert "// kept" in build._code_only(code)  # inside a string literal
+    assert build._code_only(code) != build._code_only(code.replace("a = 1", "a = 2"))
+    assert re.fullmatch(r"[0-9a-f]{16}", build.kernel_digest(build.KERNEL_FILES_CHAIN))
+
+
 def test_median_ci95():
     assert bench.median_ci95([]) == (None, [None, None])
     assert bench.median_ci95([4.0]) == (4.0, [4.0, 4.0])
