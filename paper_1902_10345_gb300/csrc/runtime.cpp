@@ -96,7 +96,10 @@ int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols
     const cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(tm, t, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, TMA2D_L2_PROMO == 64 ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
+                                                : TMA2D_L2_PROMO == 128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                                                : TMA2D_L2_PROMO == 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+                                                                        : CU_TENSOR_MAP_L2_PROMOTION_NONE,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return set_error(SDFG_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for %dx%d ld=%d", static_cast<int>(r),
