@@ -85,6 +85,13 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
+static CUtensorMapL2promotion l2_promotion(int bytes) {
+    return bytes == 64    ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
+           : bytes == 128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+           : bytes == 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+                          : CU_TENSOR_MAP_L2_PROMOTION_NONE;
+}
+
 int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols, int ld, int box_cols, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return set_error(SDFG_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
@@ -96,10 +103,7 @@ int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols
     const cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(tm, t, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, TMA2D_L2_PROMO == 64 ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
-                                                : TMA2D_L2_PROMO == 128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
-                                                : TMA2D_L2_PROMO == 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
-                                                                        : CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, l2_promotion(TMA2D_L2_PROMO),
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return set_error(SDFG_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for %dx%d ld=%d", static_cast<int>(r),
@@ -107,8 +111,9 @@ int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols
     return SDFG_OK;
 }
 
+
 int encode_tmap3d(CUtensorMap *tm, const void *base, int dtype, int depth, int rows, int cols, int ld, int box_cols,
-                  int box_rows) {
+                  int box_rows, int l2_promo) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return set_error(SDFG_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const CUtensorMapDataType t = dtype == SDFG_F64    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
@@ -121,7 +126,7 @@ int encode_tmap3d(CUtensorMap *tm, const void *base, int dtype, int depth, int r
     const cuuint32_t box[3] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(tm, t, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, l2_promotion(l2_promo),
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return set_error(SDFG_ERR_CUDA, "cuTensorMapEncodeTiled (3-D) failed (%d) for %dx%dx%d ld=%d",

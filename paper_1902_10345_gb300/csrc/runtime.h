@@ -49,9 +49,10 @@ inline int dtype_bytes(int dt) { return dt == SDFG_F64 ? 8 : (dt == SDFG_BF16 ? 
 int encode_tmap(CUtensorMap *tm, const void *base, int dtype, int rows, int cols, int ld, int box_cols,
                 int box_rows = CHUNK_ROWS);
 // Rank-3 map over a depth x rows x cols box (row pitch ld elements, plane
-// pitch rows*ld): boxes of box_cols x box_rows x 1.
+// pitch rows*ld): boxes of box_cols x box_rows x 1; l2_promo: L2 promotion
+// in bytes (0, 64, 128 or 256).
 int encode_tmap3d(CUtensorMap *tm, const void *base, int dtype, int depth, int rows, int cols, int ld, int box_cols,
-                  int box_rows);
+                  int box_rows, int l2_promo = 256);
 // True when a buffer can be read by TMA as laid out.
 inline bool tma_compatible(const void *p, int ld, int dtype) {
     return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((static_cast<long long>(ld) * dtype_bytes(dtype)) % 16 == 0);
