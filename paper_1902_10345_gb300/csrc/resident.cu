@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(RS_THREADS, 1) resident_pass_kernel(const __gr
     };
     // One step of the band from the edge rows of slot p; the new edge rows go
     // to slot p ^ 1.  CF: 0 no ring column, 1 + e ring column at element e
-    // of the lane `fixlane`, -1 the general path; RF: a ring row at band row
-    // `frow`.
+    // of the lanes with u1 set, -1 the general path; RF: a ring row at band
+    // row u0.  LAST: the pass's last step, which stores the rows.
     auto step = [&](auto cf_t, auto rf_t, auto last_t, int p) {
         constexpr int CF = decltype(cf_t)::value;
         constexpr bool RF = decltype(rf_t)::value;
