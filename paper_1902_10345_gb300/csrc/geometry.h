@@ -68,7 +68,7 @@ struct GridGeo {
 };
 
 #ifndef SDFG_F32_V
-#define SDFG_F32_V 4  // FP32 columns per lane (4 or 8)
+#define SDFG_F32_V 4  // FP32 columns per lane (the two-row reassociated pipe needs 4)
 #endif
 
 // Columns per lane for a storage size in bytes: FP32 SDFG_F32_V, BF16 4, FP64 2.
