@@ -179,6 +179,24 @@ int sdfg_jacobi2d_host(const void *h_in, void *h_out, int rows, int cols, int T,
                        void *stream);
 
 /*
+ * n independent end-to-end solves of HOST grids of one shape (h_in[i] ->
+ * T steps -> h_out[i]; contiguous, ld = cols), pipelined: solve i uses one
+ * of two device slots (input and result buffers, cached by the library)
+ * and one of two library streams, so the host<->device copies of one solve
+ * overlap the computation of the next.  Each solve copies its own input in
+ * and its own result out.  The work starts after what is already queued on
+ * `stream`, and the call returns when every h_out[i] holds its result.
+ * Results equal those of n calls of sdfg_jacobi2d_host.  h_in[i] and
+ * h_out[j] may repeat, but a buffer must not be read by one solve while
+ * another solve writes it (an output buffer reused by solves i and i+1, or
+ * an output that is also an input).  Pinned host memory gives overlapped
+ * copies; pageable memory serialises them.  SDFG_ERR_INVAL as for
+ * sdfg_jacobi2d_host, or for n < 0 or null arrays.
+ */
+int sdfg_jacobi2d_host_many(const void *const *h_in, void *const *h_out, int n, int rows, int cols, int T,
+                            int dtype, void *stream);
+
+/*
  * One solve, as used by the batch and the server.  Inputs: in, out, rows,
  * cols, ld, T (the step cap), tol, dtype.  tol = 0 runs exactly T steps.
  * tol > 0 stops at the first step t that is a multiple of the check stride
@@ -353,8 +371,8 @@ int sdfg_stats_enable(int on);
 int sdfg_stats_reset(void);
 /* Sums over launches of kernel family `name` ("naive", "temporal",
  * "persistent", "reduce", "copy", "stencil3d", "sor", "resident",
- * "skewed"), or over the host copies of sdfg_jacobi2d_host ("h2d",
- * "d2h"); waits for the recorded events. */
+ * "skewed"), or over the host copies of sdfg_jacobi2d_host and
+ * sdfg_jacobi2d_host_many ("h2d", "d2h"); waits for the recorded events. */
 int sdfg_stats_get(const char *name, long long *launches, double *total_ms);
 
 /* Reads (and with clear != 0 resets) the current device's error words: the

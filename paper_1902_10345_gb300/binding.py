@@ -52,6 +52,7 @@ _PROTOS = {
     "sdfg_jacobi2d_ex": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _VP]),
     "sdfg_jacobi2d_cfg": (_I, [_VP, _VP, _I, _I, _I, _I, _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_jacobi2d_host": (_I, [_VP, _VP, _I, _I, _I, _I, _VP]),
+    "sdfg_jacobi2d_host_many": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _VP]),
     "sdfg_jacobi2d_noalloc": (_I, [_VP, _VP, _I, _I, _I, _VP]),
     "sdfg_jacobi2d_solve": (_I, [ctypes.POINTER(sdfg_desc), _I, ctypes.POINTER(sdfg_config), _VP]),
     "sdfg_jacobi2d_batch": (_I, [ctypes.POINTER(sdfg_desc), _I, _I, _VP]),
@@ -138,6 +139,17 @@ def sdfg_jacobi2d_noalloc(inp: int, out: int, rows: int, cols: int, T: int, stre
 
 def sdfg_jacobi2d_host(h_in, h_out, rows, cols, T, dtype, stream=0) -> int:
     return lib().sdfg_jacobi2d_host(h_in, h_out, rows, cols, T, dtype, stream)
+
+
+def sdfg_jacobi2d_host_many(h_ins, h_outs, rows, cols, T, dtype, stream=0) -> int:
+    """h_ins, h_outs: sequences of host addresses (ints) of equal length."""
+    n = len(h_ins)
+    if len(h_outs) != n:
+        raise ValueError("h_ins and h_outs differ in length")
+    ins = (ctypes.c_void_p * max(n, 1))(*h_ins)
+    outs = (ctypes.c_void_p * max(n, 1))(*h_outs)
+    return lib().sdfg_jacobi2d_host_many(ctypes.cast(ins, ctypes.c_void_p), ctypes.cast(outs, ctypes.c_void_p), n,
+                                         rows, cols, T, dtype, stream)
 
 
 def sdfg_jacobi2d_solve(desc: sdfg_desc, check_stride: int, cfg: sdfg_config | None = None, stream=0) -> int:

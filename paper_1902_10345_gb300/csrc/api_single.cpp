@@ -348,3 +348,88 @@ extern "C" int sdfg_jacobi2d_host(const void *h_in, void *h_out, int rows, int c
     SDFG_CUDA(cudaStreamSynchronize(s));
     return SDFG_OK;
 }
+
+namespace {
+// Two device slots (input, result) and two streams for sdfg_jacobi2d_host_many.
+struct HostPipe {
+    std::mutex mu;
+    int device = -1;
+    size_t bytes = 0;
+    void *in[2] = {nullptr, nullptr}, *out[2] = {nullptr, nullptr};
+    cudaStream_t q[2] = {nullptr, nullptr};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // caller ready, slot 0 done, slot 1 done
+};
+HostPipe g_host_pipe;
+
+int host_pipe_ready(HostPipe &hp, int device, size_t bytes) {
+    if (!hp.q[0]) {
+        for (int i = 0; i < 2; ++i) SDFG_CUDA(cudaStreamCreateWithFlags(&hp.q[i], cudaStreamNonBlocking));
+        for (int i = 0; i < 3; ++i) SDFG_CUDA(cudaEventCreateWithFlags(&hp.ev[i], cudaEventDisableTiming));
+        hp.device = device;
+    }
+    if (hp.device != device) return set_error(SDFG_ERR_INVAL, "sdfg_jacobi2d_host_many: one device per process");
+    if (hp.bytes < bytes) {
+        SDFG_CUDA(cudaDeviceSynchronize());  // the slots may still be in use by the streams
+        for (int i = 0; i < 2; ++i) {
+            if (hp.in[i]) cudaFree(hp.in[i]);
+            if (hp.out[i]) cudaFree(hp.out[i]);
+            hp.in[i] = hp.out[i] = nullptr;
+        }
+        hp.bytes = 0;
+        for (int i = 0; i < 2; ++i) {
+            SDFG_CUDA(cudaMalloc(&hp.in[i], bytes));
+            SDFG_CUDA(cudaMalloc(&hp.out[i], bytes));
+        }
+        hp.bytes = bytes;
+    }
+    return SDFG_OK;
+}
+}  // namespace
+
+// n independent solves of host grids, pipelined: solve i runs on slot i % 2
+// (its own device input and result buffers, its own stream), so the copies
+// of one solve overlap the computation of the next.  Same operation and
+// results as n calls of sdfg_jacobi2d_host.
+extern "C" int sdfg_jacobi2d_host_many(const void *const *h_in, void *const *h_out, int n, int rows, int cols, int T,
+                                       int dtype, void *stream) {
+    if (n < 0 || (n > 0 && (!h_in || !h_out)))
+        return set_error(SDFG_ERR_INVAL, "sdfg_jacobi2d_host_many: n=%d with null arrays", n);
+    for (int i = 0; i < n; ++i) {
+        int rc = validate_grid(h_in[i], h_out[i], rows, cols, cols, T, dtype, "sdfg_jacobi2d_host_many");
+        if (rc != SDFG_OK) return rc;
+    }
+    if (n == 0 || rows == 0 || cols == 0) return SDFG_OK;
+    DeviceState *st = nullptr;
+    int rc = current_device(&st);
+    if (rc != SDFG_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = static_cast<size_t>(rows) * cols * dtype_bytes(dtype);
+    std::lock_guard<std::mutex> lk(g_host_pipe.mu);
+    HostPipe &hp = g_host_pipe;
+    rc = host_pipe_ready(hp, st->device, bytes);
+    if (rc != SDFG_OK) return rc;
+    // both slot streams start after the work already on the caller's stream
+    SDFG_CUDA(cudaEventRecord(hp.ev[0], s));
+    for (int q = 0; q < 2; ++q) SDFG_CUDA(cudaStreamWaitEvent(hp.q[q], hp.ev[0], 0));
+    for (int i = 0; i < n; ++i) {
+        const int q = i & 1;
+        cudaStream_t qs = hp.q[q];
+        TimedLaunch t_in = stats_begin(FAM_H2D, qs);
+        cudaError_t e = cudaMemcpyAsync(hp.in[q], h_in[i], bytes, cudaMemcpyHostToDevice, qs);
+        stats_end(t_in, qs);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync (host to device)");
+        rc = run_single(hp.in[q], hp.out[q], rows, cols, cols, T, dtype, nullptr, true, qs);
+        if (rc != SDFG_OK) return rc;
+        TimedLaunch t_out = stats_begin(FAM_D2H, qs);
+        e = cudaMemcpyAsync(h_out[i], hp.out[q], bytes, cudaMemcpyDeviceToHost, qs);
+        stats_end(t_out, qs);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync (device to host)");
+    }
+    // the caller's stream resumes after both slots; return when every h_out holds its result
+    for (int q = 0; q < 2; ++q) {
+        SDFG_CUDA(cudaEventRecord(hp.ev[1 + q], hp.q[q]));
+        SDFG_CUDA(cudaStreamWaitEvent(s, hp.ev[1 + q], 0));
+    }
+    SDFG_CUDA(cudaStreamSynchronize(s));
+    return SDFG_OK;
+}

@@ -209,6 +209,27 @@ def test_raw_entry_point_and_host_call():
     assert np.array_equal(ho.double().numpy(), host64(y))
 
 
+@pytest.mark.parametrize("shape,T", [((96, 160), 24), ((1100, 1300), 37)])
+def test_host_many_pipelined_equals_host_calls(shape, T):
+    """Pipelined host solves (two device slots, two streams): each result
+    equals the one-call result bit for bit, and the oracle within 1e-4; the
+    1100 x 1300 grid runs the chain kernel."""
+    R, C = shape
+    his = [torch.from_numpy(inputs.uniform_grid(R, C, seed=20 + i)).float().pin_memory() for i in range(3)]
+    hos = [torch.empty_like(h).pin_memory() for h in his]
+    stream = torch.cuda.current_stream().cuda_stream
+    binding.check(binding.sdfg_jacobi2d_host_many([h.data_ptr() for h in his], [h.data_ptr() for h in hos],
+                                                  R, C, T, F32, stream))
+    for i, (hi, ho) in enumerate(zip(his, hos)):
+        one = torch.empty_like(hi).pin_memory()
+        binding.check(binding.sdfg_jacobi2d_host(hi.data_ptr(), one.data_ptr(), R, C, T, F32, stream))
+        assert torch.equal(ho, one), i
+    want = oracle.jacobi2d(his[2].double().numpy(), T, threads=0)
+    assert np.abs(hos[2].double().numpy() - want).max() <= TOL[F32]
+    assert binding.sdfg_jacobi2d_host_many([], [], R, C, T, F32, stream) == binding.SDFG_OK
+    assert binding.sdfg_jacobi2d_host_many([his[0].data_ptr()], [0], R, C, T, F32, stream) == binding.SDFG_ERR_INVAL
+
+
 def test_full_size_8192_T1000_windows_and_properties():
     """The bench workload: 8192^2 FP32, T=1000, in the bench's launch config."""
     R = C = 8192
