@@ -401,13 +401,20 @@ def run_ours(a):
     outs = [hy.data_ptr(), hy2.data_ptr()]
     binding.check(binding.sdfg_jacobi2d_host_many(ins, outs, R, C, T, binding.SDFG_F32, stream.cuda_stream))
     barrier()
+    t0 = time.perf_counter()
+    binding.check(binding.sdfg_jacobi2d_host_many([ins[i & 1] for i in range(a.steps)],
+                                                  [outs[i & 1] for i in range(a.steps)], R, C, T,
+                                                  binding.SDFG_F32, stream.cuda_stream))
+    e2e_s = time.perf_counter() - t0
+    # the same call again, untimed, with the library's per-copy event timing
+    # on: how many copies each solve made, and how long they took
     binding.sdfg_stats_reset()
     binding.sdfg_stats_enable(True)
     t0 = time.perf_counter()
     binding.check(binding.sdfg_jacobi2d_host_many([ins[i & 1] for i in range(a.steps)],
                                                   [outs[i & 1] for i in range(a.steps)], R, C, T,
                                                   binding.SDFG_F32, stream.cuda_stream))
-    e2e_s = time.perf_counter() - t0
+    e2e_stats_s = time.perf_counter() - t0
     binding.sdfg_stats_enable(False)
     pipe_copies = {f: binding.sdfg_stats_get(f) for f in ("h2d", "d2h")}
     binding.sdfg_stats_reset()
@@ -500,8 +507,10 @@ def run_ours(a):
                        "each copying its input in and its result out, pipelined on two device slots",
                 "h2d_copies": pipe_copies["h2d"][0], "d2h_copies": pipe_copies["d2h"][0],
                 "copy_ms_per_step": (pipe_copies["h2d"][1] + pipe_copies["d2h"][1]) / a.steps,
-                "note": "copy_ms_per_step: the library's CUDA-event time of each solve's two copies, "
-                        "overlapped with the other slot's solve",
+                "ms_per_step_with_copy_timing": 1e3 * e2e_stats_s / a.steps,
+                "note": "copies counted and timed (CUDA events per copy) in a second, untimed call of the same "
+                        "K solves; copy_ms_per_step is each solve's two copies, overlapped with the other "
+                        "slot's solve",
                 "serial": {"value": e2e_serial_value, "unit": UNIT, "ms_per_step": 1e3 * e2e_serial_max / a.steps,
                            "api": "sdfg_jacobi2d_host, one call per step",
                            "copy_ms_per_step": copy_ms, "h2d_ms_per_step": h2d_ms, "d2h_ms_per_step": d2h_ms,
