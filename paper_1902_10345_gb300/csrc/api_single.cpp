@@ -359,7 +359,8 @@ struct HostPipe {
     cudaStream_t q[2] = {nullptr, nullptr};
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // caller ready, slot 0 done, slot 1 done
 };
-HostPipe g_host_pipe;
+constexpr int kHostPipeDevices = 64;
+HostPipe g_host_pipe[kHostPipeDevices];  // one pair of slots per device
 
 int host_pipe_ready(HostPipe &hp, int device, size_t bytes) {
     if (!hp.q[0]) {
@@ -367,7 +368,6 @@ int host_pipe_ready(HostPipe &hp, int device, size_t bytes) {
         for (int i = 0; i < 3; ++i) SDFG_CUDA(cudaEventCreateWithFlags(&hp.ev[i], cudaEventDisableTiming));
         hp.device = device;
     }
-    if (hp.device != device) return set_error(SDFG_ERR_INVAL, "sdfg_jacobi2d_host_many: one device per process");
     if (hp.bytes < bytes) {
         SDFG_CUDA(cudaDeviceSynchronize());  // the slots may still be in use by the streams
         for (int i = 0; i < 2; ++i) {
@@ -402,12 +402,20 @@ extern "C" int sdfg_jacobi2d_host_many(const void *const *h_in, void *const *h_o
     DeviceState *st = nullptr;
     int rc = current_device(&st);
     if (rc != SDFG_OK) return rc;
+    if (st->device < 0 || st->device >= kHostPipeDevices)
+        return set_error(SDFG_ERR_UNSUPPORTED, "sdfg_jacobi2d_host_many: device %d", st->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bytes = static_cast<size_t>(rows) * cols * dtype_bytes(dtype);
-    std::lock_guard<std::mutex> lk(g_host_pipe.mu);
-    HostPipe &hp = g_host_pipe;
+    HostPipe &hp = g_host_pipe[st->device];
+    std::lock_guard<std::mutex> lk(hp.mu);
     rc = host_pipe_ready(hp, st->device, bytes);
     if (rc != SDFG_OK) return rc;
+    // on a failure after work was queued, let that work finish (its copies
+    // read and write the caller's host buffers) before returning
+    auto fail = [&](int code) {
+        for (int q = 0; q < 2; ++q) cudaStreamSynchronize(hp.q[q]);
+        return code;
+    };
     // both slot streams start after the work already on the caller's stream
     SDFG_CUDA(cudaEventRecord(hp.ev[0], s));
     for (int q = 0; q < 2; ++q) SDFG_CUDA(cudaStreamWaitEvent(hp.q[q], hp.ev[0], 0));
@@ -417,18 +425,19 @@ extern "C" int sdfg_jacobi2d_host_many(const void *const *h_in, void *const *h_o
         TimedLaunch t_in = stats_begin(FAM_H2D, qs);
         cudaError_t e = cudaMemcpyAsync(hp.in[q], h_in[i], bytes, cudaMemcpyHostToDevice, qs);
         stats_end(t_in, qs);
-        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync (host to device)");
+        if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpyAsync (host to device)"));
         rc = run_single(hp.in[q], hp.out[q], rows, cols, cols, T, dtype, nullptr, true, qs);
-        if (rc != SDFG_OK) return rc;
+        if (rc != SDFG_OK) return fail(rc);
         TimedLaunch t_out = stats_begin(FAM_D2H, qs);
         e = cudaMemcpyAsync(h_out[i], hp.out[q], bytes, cudaMemcpyDeviceToHost, qs);
         stats_end(t_out, qs);
-        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync (device to host)");
+        if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpyAsync (device to host)"));
     }
     // the caller's stream resumes after both slots; return when every h_out holds its result
     for (int q = 0; q < 2; ++q) {
-        SDFG_CUDA(cudaEventRecord(hp.ev[1 + q], hp.q[q]));
-        SDFG_CUDA(cudaStreamWaitEvent(s, hp.ev[1 + q], 0));
+        cudaError_t e = cudaEventRecord(hp.ev[1 + q], hp.q[q]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hp.ev[1 + q], 0);
+        if (e != cudaSuccess) return fail(cuda_error(e, "sdfg_jacobi2d_host_many: stream order"));
     }
     SDFG_CUDA(cudaStreamSynchronize(s));
     return SDFG_OK;
