@@ -99,7 +99,8 @@ typedef enum {
                                    for grids that fit in L2, where a pass is
                                    latency-bound                            */
     SDFG_KERNEL_SKEWED = 5      /* one launch for all passes; each warp streams
-                                   a chain of seg_rows rows (0 = 512) of one
+                                   a chain of seg_rows rows (0: 640, 512 for
+                                   BF16 storage) of one
                                    column strip through the k fused steps,
                                    chains skewed down by k rows per pass so
                                    that no rows are recomputed between them;

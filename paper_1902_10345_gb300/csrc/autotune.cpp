@@ -108,7 +108,7 @@ extern "C" int sdfg_autotune(int rows, int cols, int T, int dtype, sdfg_config *
     // short segments give small grids enough units to fill the GPU; tall ones
     // cut the halo rows of large grids; the chain kernel takes chain lengths
     const int segs_c[] = {24, 48, 96, 128, 192};
-    const int chains_c[] = {256, 512, 1024};
+    const int chains_c[] = {256, 640, 1024};
     std::vector<sdfg_config> cands;
     // the register-resident pass is a candidate where both grids fit in L2
     // (there a pass is latency-bound, which is what it shortens)

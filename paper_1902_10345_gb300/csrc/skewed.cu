@@ -22,7 +22,7 @@
 // warp barrier.  The release waits for the warp's stores in flight, about a
 // microsecond under full HBM traffic, so publishing after every chunk costs
 // ~13% and every ~144 rows ~2%, while a longer interval adds lag from pass
-// to pass (~144 rows and 512-row chains are the measured best on 8192^2).
+// to pass (~144 rows and 640-row chains are the measured best on 8192^2).
 // Before loading input rows [r0, r0 + CR) a warp waits (bounded,
 // acquire loads) until pass p-1 has stored those rows, plus
 // e = max(0, k_{p-1} - k_p) more, in strips s-1, s, s+1 (the first wait
@@ -292,12 +292,13 @@ int chain_plan_build(ChainPlan *c, DeviceState *st, cudaStream_t s) {
 }  // namespace
 
 // The chain kernel's pass plan for T steps at depth k: plan_passes(T, k).
-// L: chain length in rows (0 = 512); pub: chunks between progress updates
+// L: chain length in rows (0: 640, 512 for BF16 storage, the measured best);
+// pub: chunks between progress updates
 // (0 = about every 144 rows).  FP32, BF16 and FP64 storage; in/out must be
 // TMA-compatible.
 int run_single_chain(const void *in, void *out, int R, int C, int ld, long long T, int dtype, int k, int L, int pub,
                      DeviceState *st, cudaStream_t s) {
-    if (L <= 0) L = 512;
+    if (L <= 0) L = dtype == SDFG_BF16 ? 512 : 640;
     if (pub <= 0) pub = chain_pub_chunks(dtype_bytes(dtype));
     L = std::max(L, 4 * k);
     std::lock_guard<std::mutex> lk(g_chain_mu);
