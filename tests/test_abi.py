@@ -126,6 +126,22 @@ def test_host_validation_sor(lib, args):
     assert binding.last_error()
 
 
+def test_host_many_validation_without_a_gpu(lib):
+    """sdfg_jacobi2d_host_many checks its arguments before touching a device:
+    a negative count, null arrays, a bad dtype or a null grid pointer are
+    rejected; no solves, or empty grids, succeed as no-ops."""
+    F32 = binding.SDFG_F32
+    assert lib.sdfg_jacobi2d_host_many(None, None, -1, 8, 8, 3, F32, None) == binding.SDFG_ERR_INVAL
+    assert lib.sdfg_jacobi2d_host_many(None, None, 2, 8, 8, 3, F32, None) == binding.SDFG_ERR_INVAL
+    assert binding.sdfg_jacobi2d_host_many([4096], [1 << 20], 8, 8, 3, 7) == binding.SDFG_ERR_INVAL
+    assert binding.sdfg_jacobi2d_host_many([4096, 8192], [1 << 20, 0], 8, 8, 3, F32) == binding.SDFG_ERR_INVAL
+    assert "sdfg_jacobi2d_host_many" in binding.last_error()
+    assert binding.sdfg_jacobi2d_host_many([], [], 8, 8, 3, F32) == binding.SDFG_OK
+    assert binding.sdfg_jacobi2d_host_many([4096], [1 << 20], 0, 8, 3, F32) == binding.SDFG_OK
+    with pytest.raises(ValueError):
+        binding.sdfg_jacobi2d_host_many([4096], [], 8, 8, 3, F32)
+
+
 def test_empty_inputs_succeed_without_a_gpu(lib):
     """Empty boxes and grids are complete no-ops (no device is touched)."""
     assert lib.sdfg_jacobi3d(None, None, 0, 5, 5, 5, 3, binding.SDFG_F32, None) == binding.SDFG_OK
